@@ -1,0 +1,458 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 255-bit NTT library.
+
+Workload (one step): forward NTT then inverse NTT of one vector of 2^20
+BLS12-381 Fr elements (uniform from seed, standard form, natural order), on
+the butterfly path, inputs resident in HBM.  Steps rotate over 8 distinct
+input vectors (768 MiB of inputs, outputs and round trips), so no step finds
+its data in the 129 MB L2.
+
+Metric: NTT field elements transformed per second (each transform of N
+elements counts N), whole job over all ranks.
+
+Printed as ONE JSON line on rank 0, with
+  * roofline: the dominant kernel (the pass kernel with the largest device
+    time) against the 32-bit integer multiply-add (IMAD) pipe:
+    algorithmic IMAD per launch = modmuls of the pass * 272 (one 8-limb CIOS
+    Montgomery product, lo and hi multiplies counted), modmuls of a pass =
+    (N/2) log2 S (radix-2 butterflies) + N (the pass's per-element multiplier
+    when it has one); peak = 152 SMs * 64 IMAD/clk * 2.07 GHz;
+  * e2e: the same metric through ntt_transform_host (pinned host buffers,
+    host-to-device and device-to-host copies inside the timed region);
+  * cpu_baseline: the C oracle on this host's cores (single-threaded) on a
+    bounded sample of the same workload;
+  * secondary: the 2^24-point BLS12-381 forward NTT (elements/s and IMAD
+    roofline fraction of the whole transform);
+  * clocks: nvidia-smi samples taken during the timed region.
+
+``--impl reference`` times the oracle instead (rank 0 only), the baseline
+the driver compares against.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from ntt_synth import config_seed, uniform_elements  # noqa: E402
+
+METRIC = "255-bit NTT field elements/s (BLS12-381 Fr, n=2^20, forward+inverse, butterfly path)"
+UNIT = "elements/s"
+IMAD_PER_MODMUL = 272
+SMS = 152
+IMAD_PER_CLK_PER_SM = 64
+SM_MAX_MHZ = 2070.0
+FIELD = "bls12_381_fr"
+LOG_N = 20
+ROTATE = 8
+L2_NOTE = "inputs larger than L2: 8 rotating 2^20 vectors (in, out, round trip: 768 MiB)"
+
+
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def imad_peak_tops() -> float:
+    """Tera IMAD/s: SMs x IMAD lanes per clock x maximum SM clock."""
+    mhz = peaks().get("sm_max_mhz", SM_MAX_MHZ)
+    return SMS * IMAD_PER_CLK_PER_SM * mhz * 1e6 / 1e12
+
+
+def pass_modmuls(log_n: int, pass_log: list[int], j: int, has_multiplier: bool) -> int:
+    n = 1 << log_n
+    return (n // 2) * pass_log[j] + (n if has_multiplier else 0)
+
+
+def transform_modmuls(log_n: int) -> int:
+    """Algorithmic modmuls of one transform: (N/2) log2 N butterflies + 2N."""
+    n = 1 << log_n
+    return (n // 2) * log_n + 2 * n
+
+
+# ----------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.close()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for r in csv.reader(fh):
+                if len(r) >= 9:
+                    rows.append([c.strip() for c in r])
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------ distributed
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, backend: str):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend=backend)
+
+
+def dist_max(value: float, world: int, device) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------- our arm
+
+
+def to_dev(torch, a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def timed_loop(torch, N, plan, bufs, steps: int, stream) -> float:
+    """Time `steps` forward+inverse steps with CUDA events on `stream`; ms."""
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(steps):
+        x, y, z = bufs[i % len(bufs)]
+        N.ntt_forward(plan, x, y, stream)
+        N.ntt_inverse(plan, y, z, stream)
+    stop.record(stream)
+    stop.synchronize()
+    return start.elapsed_time(stop)
+
+
+def golden_digest(kind: str) -> str | None:
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_digests.json")) as fh:
+            for c in json.load(fh)["single"]:
+                if c["config"] == 2 and c["kind"] == kind:
+                    return c["output_sha256"]
+    except OSError:
+        return None
+    return None
+
+
+def measure_2_24(torch, N, stream, steps: int) -> dict:
+    log_n = 24
+    plan = N.ntt_plan_create(FIELD, log_n)
+    try:
+        desc = N.ntt_plan_describe(plan)
+        xs = [to_dev(torch, uniform_elements(FIELD, 1 << log_n, config_seed(3, 200 + r))) for r in range(2)]
+        ys = [torch.empty_like(x) for x in xs]
+        for i in range(2):
+            N.ntt_forward(plan, xs[i], ys[i], stream)
+        torch.cuda.synchronize()
+        N.ntt_plan_enable_timing(plan, True)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for i in range(steps):
+            N.ntt_forward(plan, xs[i % 2], ys[i % 2], stream)
+        stop.record(stream)
+        stop.synchronize()
+        ms = start.elapsed_time(stop) / steps
+        pass_ms, pass_cnt = N.ntt_plan_read_timing(plan)
+        N.ntt_plan_enable_timing(plan, False)
+        peak = imad_peak_tops()
+        alg = transform_modmuls(log_n) * IMAD_PER_MODMUL
+        per_pass = []
+        for j, ls in enumerate(desc["pass_log"]):
+            avg = pass_ms[j] / max(1, pass_cnt[j])
+            mm = pass_modmuls(log_n, desc["pass_log"], j, j >= 1)
+            per_pass.append({"pass": j, "log_s": ls, "avg_ms": round(avg, 4),
+                             "frac": round(mm * IMAD_PER_MODMUL / (avg * 1e-3) / 1e12 / peak, 4)})
+        return {"workload": "BLS12-381 Fr forward NTT, n=2^24, butterfly path", "ms": round(ms, 4),
+                "elements_per_s": (1 << log_n) / (ms * 1e-3),
+                "imad_roofline_frac": round(alg / (ms * 1e-3) / 1e12 / peak, 4), "passes": per_pass}
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
+def measure_e2e(torch, N, plan, x_host: np.ndarray, steps: int, stream) -> dict:
+    n = x_host.shape[0]
+    h_in = torch.from_numpy(x_host.view(np.int64)).pin_memory()
+    h_mid = torch.empty_like(h_in).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_work = torch.empty(h_in.shape, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        N.ntt_transform_host(plan, "forward", h_in, h_mid, d_work, stream)
+        N.ntt_transform_host(plan, "inverse", h_mid, h_out, d_work, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        N.ntt_transform_host(plan, "forward", h_in, h_mid, d_work, stream)
+        N.ntt_transform_host(plan, "inverse", h_mid, h_out, d_work, stream)
+    dt = time.perf_counter() - t0
+    ok = bool(torch.equal(h_out, h_in))
+    return {"value": 2 * n * steps / dt, "unit": UNIT, "h2d_bytes_per_step": 2 * 32 * n,
+            "d2h_bytes_per_step": 2 * 32 * n, "round_trip_exact": ok}
+
+
+def cpu_baseline(x: np.ndarray, budget_s: float = 12.0) -> dict:
+    import oracle
+
+    n = x.shape[0]
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        y = oracle.c_transform(FIELD, "forward", x)
+        oracle.c_transform(FIELD, "inverse", y)
+        done += 2 * n
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"C oracle (single-threaded), forward+inverse of the 2^{n.bit_length() - 1} "
+                      f"BLS12-381 workload vector, {done // (2 * n)} round(s) in {dt:.1f} s"}
+
+
+def run_ours(args) -> None:
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    from paper_2604_17808_gb300 import _native as N
+
+    N.load(build_if_missing=True)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    log_n = args.log_n
+    n = 1 << log_n
+    plan = N.ntt_plan_create(FIELD, log_n)
+    desc = N.ntt_plan_describe(plan)
+    host_inputs = [uniform_elements(FIELD, n, config_seed(2, 1000 * rank + r) if r else config_seed(2))
+                   for r in range(ROTATE)]
+    bufs = []
+    for h in host_inputs:
+        x = to_dev(torch, h)
+        bufs.append((x, torch.empty_like(x), torch.empty_like(x)))
+    # parity of the first step against the stored oracle digests (same seed as the tests)
+    parity = None
+    if log_n == LOG_N and rank == 0:
+        N.ntt_forward(plan, bufs[0][0], bufs[0][1], stream)
+        N.ntt_inverse(plan, bufs[0][0], bufs[0][2], stream)
+        torch.cuda.synchronize()
+        f = hashlib.sha256(bufs[0][1].cpu().numpy().astype("<i8").tobytes()).hexdigest()
+        i = hashlib.sha256(bufs[0][2].cpu().numpy().astype("<i8").tobytes()).hexdigest()
+        parity = (f == golden_digest("forward")) and (i == golden_digest("inverse"))
+    for _ in range(args.warmup):
+        timed_loop(torch, N, plan, bufs, 1, stream)
+    torch.cuda.synchronize()
+
+    N.ntt_plan_enable_timing(plan, True)
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local).start() if rank == 0 else None
+    ms = timed_loop(torch, N, plan, bufs, args.steps, stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    dist_barrier(world)
+    pass_ms, pass_cnt = N.ntt_plan_read_timing(plan)
+    N.ntt_plan_enable_timing(plan, False)
+    ms_max = dist_max(ms, world, device)
+
+    # correctness of the timed steps: the round trip must give the input back
+    round_trip_ok = all(bool(torch.equal(z, x)) for x, _, z in bufs)
+
+    elements = 2 * n * args.steps * world
+    value = elements / (ms_max * 1e-3)
+    peak = imad_peak_tops()
+    dom = max(range(desc["num_passes"]), key=lambda j: pass_ms[j])
+    avg_ms = pass_ms[dom] / max(1, pass_cnt[dom])
+    mm = pass_modmuls(log_n, desc["pass_log"], dom, dom >= 1)
+    achieved = mm * IMAD_PER_MODMUL / (avg_ms * 1e-3) / 1e12
+    launches = args.steps * 2 * desc["launches_per_transform"]
+
+    secondary = None
+    e2e = None
+    cpu = None
+    if rank == 0:
+        e2e = measure_e2e(torch, N, plan, host_inputs[0], max(3, args.steps // 4), stream)
+        if not args.quick:
+            secondary = measure_2_24(torch, N, stream, steps=max(3, args.steps // 4))
+        if world == 1 and not args.no_cpu:
+            cpu = cpu_baseline(host_inputs[0])
+    N.ntt_plan_destroy(plan)
+    if rank != 0:
+        dist_barrier(world)
+        return
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (uniform field elements from seed, SplitMix64)",
+        "config": {"workload": f"BLS12-381 Fr NTT n=2^{log_n}, forward+inverse per step, butterfly path "
+                               f"(passes {desc['pass_log']})",
+                   "field": FIELD, "log_n": log_n, "transforms_per_step": 2, "per_rank_vectors": ROTATE,
+                   "l2": L2_NOTE, "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T IMAD/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": f"ntt_pass_kernel pass {dom} (S=2^{desc['pass_log'][dom]})",
+                     "avg_launch_ms": avg_ms,
+                     "peak_note": "152 SMs x 64 IMAD/clk x 2070 MHz (unit counts and maximum clock)"},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "parity": {"first_step_matches_oracle_digest": parity, "round_trip_exact": round_trip_ok},
+        "pass_ms_total": [round(v, 4) for v in pass_ms[: desc["num_passes"]]],
+        "secondary": secondary,
+        "paths": {"butterfly": value, "matrix": None},
+    }
+    print(json.dumps(line), flush=True)
+    dist_barrier(world)
+
+
+# ----------------------------------------------------- reference arm
+
+
+def run_reference(args) -> None:
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.c_oracle()
+    # calibrate, then pick the largest sample (<= 2^20) that keeps the run short
+    probe = uniform_elements(FIELD, 1 << 14, config_seed(2))
+    t0 = time.perf_counter()
+    oracle.c_transform(FIELD, "forward", probe)
+    per_elem_log = (time.perf_counter() - t0) / ((1 << 14) * 14)
+    total_steps = args.steps + args.warmup
+    log_s = LOG_N
+    while log_s > 12 and total_steps * 2 * per_elem_log * (1 << log_s) * log_s > 150.0:
+        log_s -= 1
+    x = uniform_elements(FIELD, 1 << LOG_N, config_seed(2))[: 1 << log_s].copy()
+    for _ in range(args.warmup):
+        oracle.c_transform(FIELD, "inverse", oracle.c_transform(FIELD, "forward", x))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.c_transform(FIELD, "inverse", oracle.c_transform(FIELD, "forward", x))
+    dt = time.perf_counter() - t0
+    value = 2 * (1 << log_s) * args.steps / dt
+    sample = (f"C oracle (single-threaded), forward+inverse of the first 2^{log_s} elements of the 2^20 "
+              f"workload vector per step")
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic (uniform field elements from seed, SplitMix64)",
+        "config": {"workload": f"BLS12-381 Fr NTT n=2^{LOG_N}, forward+inverse per step (oracle on a 2^{log_s} "
+                               f"sample)", "field": FIELD, "log_n": LOG_N, "sample_log_n": log_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log-n", type=int, default=LOG_N)
+    ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

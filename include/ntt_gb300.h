@@ -1,0 +1,217 @@
+/*
+ * ntt_gb300.h -- C ABI of the GB300 (sm_103a) 255-bit number-theoretic
+ * transform library.
+ *
+ * The operation (MORPH, Sec. 2.3.1, "Number Theory Transformation"): for a
+ * vector x of N = 2^log_n elements of the prime field F_M,
+ *
+ *     forward:  X_k = sum_{n<N} x_n * omega_N^{k n}            mod M
+ *     inverse:  x_n = N^{-1} * sum_{k<N} X_k * omega_N^{-k n}   mod M
+ *     coset:    X_k = sum_{n<N} x_n * (s * omega_N^k)^n          mod M
+ *
+ * with omega_N = g^((M-1)/N), g the field's multiplicative generator (7 for
+ * BLS12-381 Fr, 5 for BN254 Fr) and s the coset shift (default g).  The
+ * paper states the forward transform; inverse and coset are the standard
+ * companions of a prover's evaluation / interpolation step.  The results are
+ * exact: no rounding, outputs canonical in [0, M).
+ *
+ * Data layout (every buffer, host or device): N elements, element i at byte
+ * offset 32*i, each element four little-endian uint64 limbs (limb 0 least
+ * significant), standard (not Montgomery) representation, canonical in
+ * [0, M), natural order in and out.  Device buffers must be 16-byte aligned.
+ *
+ * Ownership: the caller owns every input and output buffer.  A plan owns its
+ * device-resident twiddle tables and one scratch vector of N elements, all
+ * allocated by ntt_plan_create on the current CUDA device and freed by
+ * ntt_plan_destroy.
+ *
+ * Streams and asynchrony: ntt_forward / ntt_inverse / ntt_coset_forward /
+ * ntt_batch_submit only enqueue work on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream) and return without synchronising.  Their status
+ * covers argument and launch errors only.  Errors detected on the device
+ * (a bounded wait that ran out, see ntt_batch_submit) are read afterwards
+ * with ntt_plan_poll_error / ntt_batch_poll_error.
+ *
+ * Concurrency: a plan is immutable after creation (except the two setters
+ * below, which must not race with transforms).  Out-of-place transforms
+ * (in != out) on one plan may run concurrently on several streams.  In-place
+ * transforms (in == out) with more than one pass use the plan's scratch
+ * vector, so concurrent in-place transforms on one plan race: order them on
+ * one stream or use one plan per stream.
+ *
+ * Errors: every call returns an ntt_status; NTT_ERR_INVALID_ARG for a NULL
+ * plan or buffer, a misaligned buffer or an unknown enum value;
+ * NTT_ERR_UNSUPPORTED for log_n outside [1, min(2-adicity, 28)];
+ * NTT_ERR_OOM when a device allocation fails; NTT_ERR_CUDA for any other CUDA
+ * runtime error (the CUDA error is kept by the runtime as usual).  Inputs
+ * must be canonical (< M): non-canonical inputs are a precondition violation
+ * and give unspecified (but memory-safe) outputs.
+ */
+#ifndef NTT_GB300_H
+#define NTT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *ntt_stream;
+
+typedef enum ntt_status {
+    NTT_OK = 0,
+    NTT_ERR_INVALID_ARG = 1,
+    NTT_ERR_UNSUPPORTED = 2,
+    NTT_ERR_OOM = 3,
+    NTT_ERR_CUDA = 4,
+    NTT_ERR_TIMEOUT = 5,   /* a device-side bounded wait ran out */
+    NTT_ERR_BUDGET = 6,    /* a memory budget would be exceeded */
+    NTT_ERR_NO_DEVICE = 7  /* no usable CUDA device of compute capability 10.3 */
+} ntt_status;
+
+typedef enum ntt_field {
+    NTT_FIELD_BLS12_381_FR = 0, /* r = 0x73eda753...ffffffff00000001, 255 bits, 2-adicity 32, g = 7 */
+    NTT_FIELD_BN254_FR = 1      /* r = 0x30644e72...43e1f593f0000001, 254 bits, 2-adicity 28, g = 5 */
+} ntt_field;
+
+typedef enum ntt_kind {
+    NTT_KIND_FORWARD = 0,
+    NTT_KIND_INVERSE = 1,
+    NTT_KIND_COSET = 2      /* coset forward */
+} ntt_kind;
+
+typedef enum ntt_path {
+    NTT_PATH_AUTO = 0,      /* the library's choice (butterfly passes) */
+    NTT_PATH_BUTTERFLY = 1, /* radix-2^k shared-memory butterfly passes on 32-bit IMAD (Fig. 4a) */
+    NTT_PATH_MATRIX = 2     /* matrix-form column DFT on tensor cores (Sec. 3.3.2, Alg. 2 ByteDecompose/Einsum/ByteMerge) */
+} ntt_path;
+
+typedef struct ntt_plan_s *ntt_plan;
+
+/*
+ * Create a plan for N = 2^log_n elements of `field` on the current CUDA
+ * device.  Builds (on the device) the twiddle tables of the forward and the
+ * inverse transform, and of the coset transform when `coset` is nonzero
+ * (shift = the field's generator), and allocates the scratch vector.
+ * Cost: a few milliseconds plus about (3 + coset) * 32 * N bytes of device
+ * memory.  On success *out holds the plan; on failure *out is NULL.
+ */
+ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int coset);
+
+/* Choose the path used by later transforms on this plan. */
+ntt_status ntt_plan_set_path(ntt_plan plan, ntt_path path);
+
+/*
+ * Replace the coset shift s (four little-endian limbs, canonical, nonzero)
+ * and rebuild the coset tables.  Synchronous.  Requires a plan created with
+ * coset != 0.
+ */
+ntt_status ntt_plan_set_coset_shift(ntt_plan plan, const uint64_t shift[4]);
+
+/* Free the plan's device memory.  Waits for the device first.  NULL is OK. */
+ntt_status ntt_plan_destroy(ntt_plan plan);
+
+/*
+ * The three transforms, device buffers, stream-ordered.  d_in and d_out hold
+ * N elements each (layout above); d_in == d_out (in place) is allowed.
+ */
+ntt_status ntt_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream);
+ntt_status ntt_inverse(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream);
+ntt_status ntt_coset_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream);
+
+/* Same as the three calls above, with the kind as an argument. */
+ntt_status ntt_execute(ntt_plan plan, ntt_kind kind, const void *d_in, void *d_out, ntt_stream stream);
+
+/*
+ * End-to-end transform of HOST buffers: copies h_in (N elements) to the
+ * device buffer d_work (N elements, caller-owned), transforms it in place and
+ * copies the result to h_out, all on `stream`, then synchronises the stream.
+ * Host buffers should be page-locked for the copies to be asynchronous.
+ */
+ntt_status ntt_transform_host(ntt_plan plan, ntt_kind kind, const void *h_in, void *h_out,
+                              void *d_work, ntt_stream stream);
+
+/*
+ * Read back the plan's structure: number of passes, the log2 size of each
+ * pass's sub-transforms (up to 4), and the number of kernel launches one
+ * transform makes.
+ */
+typedef struct ntt_plan_desc {
+    uint32_t field;
+    uint32_t log_n;
+    uint32_t num_passes;
+    uint32_t pass_log[4];
+    uint32_t launches_per_transform;
+    uint32_t path;
+    uint64_t device_bytes;
+} ntt_plan_desc;
+ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out);
+
+/*
+ * Copy `count` entries (from entry `first`) of one device twiddle table to
+ * host memory, converted to standard form, so that tests can check the
+ * tables against an independent computation.  table: 0 = the DFT twiddles
+ * omega_S^i (i < S/2) of pass `pass`'s sub-transform size S; 1 = the input
+ * multipliers of pass `pass` (pass >= 1: omega_M^{n q} [times s^{...} and
+ * N^-1 folded in], row-major [n][q]; pass 0: the coset / scale factors).
+ * Synchronous.
+ */
+ntt_status ntt_plan_read_table(ntt_plan plan, ntt_kind kind, uint32_t pass, uint32_t table,
+                               uint64_t first, uint64_t count, void *h_out);
+
+/*
+ * Batched submission: many independent transforms of possibly different
+ * sizes and fields in one persistent kernel launch.  jobs[i].plan fixes field
+ * and size; kind is an ntt_kind; in/out are device buffers as above (in-place
+ * jobs are rejected with NTT_ERR_INVALID_ARG: the batched path has no
+ * scratch).  Stream-ordered.
+ */
+typedef struct ntt_job {
+    ntt_plan plan;
+    int32_t kind;
+    const void *in;
+    void *out;
+} ntt_job;
+ntt_status ntt_batch_submit(const ntt_job *jobs, size_t n, ntt_stream stream);
+
+/*
+ * Per-pass launch timing.  While enabled, every pass launch of this plan's
+ * transforms is bracketed by two CUDA events recorded on the launch's own
+ * stream.  ntt_plan_read_timing synchronises those events and returns, per
+ * pass (up to 4), the summed device time in milliseconds and the number of
+ * launches timed since the last read, then clears the record.  Timing adds
+ * two event records per launch; leave it off outside measurements.
+ */
+ntt_status ntt_plan_enable_timing(ntt_plan plan, int enable);
+ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[4], uint64_t launches_per_pass[4]);
+
+/*
+ * Device-detected error of the plan's last transforms (0 = none), cleared on
+ * read.  Synchronises the device.
+ */
+ntt_status ntt_plan_poll_error(ntt_plan plan, uint32_t *code);
+
+/*
+ * Diagnostic: element-wise Montgomery product of device vectors,
+ * out[i] = a[i] * b[i] * 2^-256 mod M, the field multiplication every
+ * butterfly uses (the paper's "radix Mont" baseline, Sec. 2.3.2: 8 32-bit
+ * digits, O(D^2) product and Montgomery reduction).  count elements each,
+ * layout as above, inputs canonical.  Stream-ordered.
+ */
+ntt_status ntt_field_mont_mul(ntt_field field, const void *d_a, const void *d_b, void *d_out, uint64_t count,
+                              ntt_stream stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *ntt_status_string(ntt_status status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+uint32_t ntt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTT_GB300_H */

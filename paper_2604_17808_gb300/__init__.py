@@ -1,0 +1,85 @@
+"""GB300 (sm_103a) 255-bit number-theoretic transform library.
+
+The compute path is libntt_gb300.so (hand-written CUDA, C ABI in
+include/ntt_gb300.h); this package is its thin Python binding:
+
+  * ``_native``  -- ctypes wrappers named like the C calls;
+  * ``_build``   -- the nvcc build of the library;
+  * ``Plan``     -- a small owner object over a plan handle for torch users.
+
+Importing the package does not load CUDA; the first call does, and raises if
+the library has not been built.
+"""
+
+from __future__ import annotations
+
+from . import _build, _native  # noqa: F401
+from ._native import (  # noqa: F401
+    FIELD,
+    KIND,
+    PATH,
+    NttError,
+    ntt_batch_submit,
+    ntt_coset_forward,
+    ntt_execute,
+    ntt_field_mont_mul,
+    ntt_forward,
+    ntt_inverse,
+    ntt_plan_create,
+    ntt_plan_describe,
+    ntt_plan_destroy,
+    ntt_plan_poll_error,
+    ntt_plan_read_table,
+    ntt_plan_set_coset_shift,
+    ntt_plan_set_path,
+    ntt_status_string,
+    ntt_transform_host,
+    ntt_version,
+)
+
+
+class Plan:
+    """Owns one ntt_plan handle; buffers are torch int64 tensors of shape [N, 4]."""
+
+    def __init__(self, field, log_n: int, coset: bool = False, path: str | None = None):
+        self.field = field
+        self.log_n = int(log_n)
+        self.n = 1 << self.log_n
+        self.handle = ntt_plan_create(field, self.log_n, coset)
+        if path is not None:
+            ntt_plan_set_path(self.handle, path)
+
+    def run(self, kind, x, out=None, stream=None):
+        if out is None:
+            out = x.new_empty(x.shape)
+        ntt_execute(self.handle, kind, x, out, stream)
+        return out
+
+    def forward(self, x, out=None, stream=None):
+        return self.run("forward", x, out, stream)
+
+    def inverse(self, x, out=None, stream=None):
+        return self.run("inverse", x, out, stream)
+
+    def coset_forward(self, x, out=None, stream=None):
+        return self.run("coset", x, out, stream)
+
+    def describe(self) -> dict:
+        return ntt_plan_describe(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            ntt_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

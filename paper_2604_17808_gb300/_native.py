@@ -1,0 +1,232 @@
+"""ctypes binding of libntt_gb300.so (the C ABI declared in include/ntt_gb300.h).
+
+Argument marshalling only: every step of a transform runs in the library's
+CUDA kernels.  Buffers may be given as integers (raw device / host addresses)
+or as objects with ``data_ptr()`` (torch tensors); streams as integers (a
+cudaStream_t value), objects with ``cuda_stream`` (torch.cuda.Stream) or None
+(legacy default stream).  The library must have been built (``_build.build``);
+loading fails loudly otherwise -- there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import _build
+
+NTT_OK = 0
+STATUS_NAMES = {
+    0: "NTT_OK", 1: "NTT_ERR_INVALID_ARG", 2: "NTT_ERR_UNSUPPORTED", 3: "NTT_ERR_OOM",
+    4: "NTT_ERR_CUDA", 5: "NTT_ERR_TIMEOUT", 6: "NTT_ERR_BUDGET", 7: "NTT_ERR_NO_DEVICE",
+}
+FIELD = {"bls12_381_fr": 0, "bn254_fr": 1}
+KIND = {"forward": 0, "inverse": 1, "coset": 2}
+PATH = {"auto": 0, "butterfly": 1, "matrix": 2}
+HEADER = os.path.join(_build.ROOT, "include", "ntt_gb300.h")
+
+
+class NttError(RuntimeError):
+    def __init__(self, status: int, call: str):
+        self.status = status
+        super().__init__(f"{call} failed: {STATUS_NAMES.get(status, status)}")
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("field", ctypes.c_uint32), ("log_n", ctypes.c_uint32), ("num_passes", ctypes.c_uint32),
+        ("pass_log", ctypes.c_uint32 * 4), ("launches_per_transform", ctypes.c_uint32),
+        ("path", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
+    ]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("kind", ctypes.c_int32), ("in_", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_SIGS = {
+    "ntt_plan_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _U32, ctypes.c_int]),
+    "ntt_plan_set_path": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "ntt_plan_set_coset_shift": (ctypes.c_int, [_VP, ctypes.POINTER(_U64)]),
+    "ntt_plan_destroy": (ctypes.c_int, [_VP]),
+    "ntt_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ntt_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ntt_coset_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ntt_execute": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "ntt_transform_host": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "ntt_plan_describe": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc)]),
+    "ntt_plan_read_table": (ctypes.c_int, [_VP, ctypes.c_int, _U32, _U32, _U64, _U64, _VP]),
+    "ntt_batch_submit": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP]),
+    "ntt_plan_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
+    "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
+    "ntt_plan_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "ntt_plan_read_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U64)]),
+    "ntt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ntt_version": (_U32, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libntt_gb300.so; raise if it is not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build the CUDA library first (__graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/ntt_gb300.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ntt_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "__array_interface__"):
+        return int(x.__array_interface__["data"][0])
+    return int(x)
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    return int(s)
+
+
+def _check(status: int, call: str) -> None:
+    if status != NTT_OK:
+        raise NttError(status, call)
+
+
+def _field(f) -> int:
+    return FIELD[f] if isinstance(f, str) else int(f)
+
+
+def _kind(k) -> int:
+    return KIND[k] if isinstance(k, str) else int(k)
+
+
+# ----------------------------------------------------------- the C ABI calls
+
+
+def ntt_plan_create(field, log_n: int, coset: bool = False) -> int:
+    h = _VP()
+    _check(load().ntt_plan_create(ctypes.byref(h), _field(field), int(log_n), 1 if coset else 0), "ntt_plan_create")
+    return int(h.value)
+
+
+def ntt_plan_set_path(plan: int, path) -> None:
+    p = PATH[path] if isinstance(path, str) else int(path)
+    _check(load().ntt_plan_set_path(plan, p), "ntt_plan_set_path")
+
+
+def ntt_plan_set_coset_shift(plan: int, shift: int) -> None:
+    arr = (_U64 * 4)(*[(shift >> (64 * i)) & (2**64 - 1) for i in range(4)])
+    _check(load().ntt_plan_set_coset_shift(plan, arr), "ntt_plan_set_coset_shift")
+
+
+def ntt_plan_destroy(plan: int) -> None:
+    _check(load().ntt_plan_destroy(plan), "ntt_plan_destroy")
+
+
+def ntt_forward(plan: int, d_in, d_out, stream=None) -> None:
+    _check(load().ntt_forward(plan, _ptr(d_in), _ptr(d_out), _stream(stream)), "ntt_forward")
+
+
+def ntt_inverse(plan: int, d_in, d_out, stream=None) -> None:
+    _check(load().ntt_inverse(plan, _ptr(d_in), _ptr(d_out), _stream(stream)), "ntt_inverse")
+
+
+def ntt_coset_forward(plan: int, d_in, d_out, stream=None) -> None:
+    _check(load().ntt_coset_forward(plan, _ptr(d_in), _ptr(d_out), _stream(stream)), "ntt_coset_forward")
+
+
+def ntt_execute(plan: int, kind, d_in, d_out, stream=None) -> None:
+    _check(load().ntt_execute(plan, _kind(kind), _ptr(d_in), _ptr(d_out), _stream(stream)), "ntt_execute")
+
+
+def ntt_transform_host(plan: int, kind, h_in, h_out, d_work, stream=None) -> None:
+    _check(load().ntt_transform_host(plan, _kind(kind), _ptr(h_in), _ptr(h_out), _ptr(d_work), _stream(stream)),
+           "ntt_transform_host")
+
+
+def ntt_plan_describe(plan: int) -> dict:
+    d = PlanDesc()
+    _check(load().ntt_plan_describe(plan, ctypes.byref(d)), "ntt_plan_describe")
+    return {"field": d.field, "log_n": d.log_n, "num_passes": d.num_passes,
+            "pass_log": list(d.pass_log)[: d.num_passes], "launches_per_transform": d.launches_per_transform,
+            "path": d.path, "device_bytes": d.device_bytes}
+
+
+def ntt_plan_read_table(plan: int, kind, pass_index: int, table: int, first: int, count: int, h_out) -> None:
+    _check(load().ntt_plan_read_table(plan, _kind(kind), pass_index, table, first, count, _ptr(h_out)),
+           "ntt_plan_read_table")
+
+
+def ntt_batch_submit(jobs, stream=None) -> None:
+    """jobs: iterable of (plan, kind, d_in, d_out)."""
+    jobs = list(jobs)
+    arr = (Job * max(1, len(jobs)))()
+    for i, (plan, kind, d_in, d_out) in enumerate(jobs):
+        arr[i] = Job(plan, _kind(kind), _ptr(d_in), _ptr(d_out))
+    _check(load().ntt_batch_submit(arr, len(jobs), _stream(stream)), "ntt_batch_submit")
+
+
+def ntt_plan_poll_error(plan: int) -> int:
+    code = _U32()
+    _check(load().ntt_plan_poll_error(plan, ctypes.byref(code)), "ntt_plan_poll_error")
+    return int(code.value)
+
+
+def ntt_field_mont_mul(field, d_a, d_b, d_out, count: int, stream=None) -> None:
+    _check(load().ntt_field_mont_mul(_field(field), _ptr(d_a), _ptr(d_b), _ptr(d_out), int(count), _stream(stream)),
+           "ntt_field_mont_mul")
+
+
+def ntt_plan_enable_timing(plan: int, enable: bool = True) -> None:
+    _check(load().ntt_plan_enable_timing(plan, 1 if enable else 0), "ntt_plan_enable_timing")
+
+
+def ntt_plan_read_timing(plan: int) -> tuple[list[float], list[int]]:
+    """(summed ms per pass, launches per pass) since the last read."""
+    ms = (ctypes.c_double * 4)()
+    cnt = (_U64 * 4)()
+    _check(load().ntt_plan_read_timing(plan, ms, cnt), "ntt_plan_read_timing")
+    return list(ms), list(cnt)
+
+
+def ntt_status_string(status: int) -> str:
+    return load().ntt_status_string(int(status)).decode()
+
+
+def ntt_version() -> int:
+    return int(load().ntt_version())

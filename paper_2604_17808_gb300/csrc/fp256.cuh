@@ -1,0 +1,245 @@
+// fp256.cuh -- 255-bit prime-field arithmetic for sm_103a, 8 x 32-bit limbs.
+//
+// The paper's arithmetic baseline ("radix Mont", Sec. 2.3.2 and Tab. 2): a
+// field element is D = 8 32-bit digits; a multiplication is an O(D^2) digit
+// product with carry propagation followed by an O(D^2) Montgomery reduction.
+// On a GPU the carry chains are native (mad.lo.cc / madc.hi.cc on the
+// integer multiply-add pipe), so this is the hot loop of the butterfly path.
+//
+// Conventions used throughout the library:
+//   * element = uint32_t[8], limb 0 least significant;
+//   * data stays in STANDARD form end to end; every constant operand
+//     (twiddles, coset powers, N^-1) is stored in MONTGOMERY form c*2^256, so
+//     mont_mul(x, c*2^256) = x*c mod p is again standard.  No conversion
+//     passes are needed at the ABI boundary;
+//   * every value is canonical in [0, p) before and after each operation.
+//
+// mont_mul is the coarsely integrated operand scanning (CIOS) form of
+// Montgomery multiplication (Koc, Acar, Kaliski, "Analyzing and comparing
+// Montgomery multiplication algorithms", IEEE Micro 1996), radix 2^32.  With
+// a, b < p < 2^255 the running value stays below 2^288, so it fits in nine
+// limbs and the last carry of every row is provably zero.
+#pragma once
+
+#include <cstdint>
+
+namespace gb300ntt {
+
+constexpr uint32_t neg_inv_u32(uint32_t p0) {
+  // Newton iteration for p0^-1 mod 2^32 (p0 odd); each step doubles the
+  // number of correct low bits, starting from 3 (p0 * p0 = 1 mod 8).
+  uint32_t inv = p0;
+  for (int i = 0; i < 5; ++i) inv *= 2u - p0 * inv;
+  return 0u - inv;
+}
+
+// BLS12-381 scalar field r (255 bits, 2-adicity 32, generator 7).
+struct FieldBls12381Fr {
+  static constexpr int kId = 0;
+  static constexpr uint32_t P0 = 0x00000001u, P1 = 0xffffffffu, P2 = 0xfffe5bfeu, P3 = 0x53bda402u,
+                            P4 = 0x09a1d805u, P5 = 0x3339d808u, P6 = 0x299d7d48u, P7 = 0x73eda753u;
+  static constexpr uint32_t NP = neg_inv_u32(P0);
+};
+
+// BN254 scalar field r (254 bits, 2-adicity 28, generator 5).
+struct FieldBn254Fr {
+  static constexpr int kId = 1;
+  static constexpr uint32_t P0 = 0xf0000001u, P1 = 0x43e1f593u, P2 = 0x79b97091u, P3 = 0x2833e848u,
+                            P4 = 0x8181585du, P5 = 0xb85045b6u, P6 = 0xe131a029u, P7 = 0x30644e72u;
+  static constexpr uint32_t NP = neg_inv_u32(P0);
+};
+
+static_assert(FieldBls12381Fr::P0 * (0u - FieldBls12381Fr::NP) == 1u, "NP");
+static_assert(FieldBn254Fr::P0 * (0u - FieldBn254Fr::NP) == 1u, "NP");
+
+// ------------------------------------------------------------------ helpers
+
+// t[0..8] += lo(a[j] * b) at limb j, carry into t[8].
+__device__ __forceinline__ void row_lo(uint32_t t[9], const uint32_t a[8], uint32_t b) {
+  asm("mad.lo.cc.u32  %0, %9,  %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;"
+      : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+        "+r"(t[8])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b));
+}
+
+// t[1..8] += hi(a[j] * b) at limb j+1 (no carry out: bounded, see header).
+__device__ __forceinline__ void row_hi(uint32_t t[9], const uint32_t a[8], uint32_t b) {
+  asm("mad.hi.cc.u32  %0, %8,  %16, %0;\n\t"
+      "madc.hi.cc.u32 %1, %9,  %16, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %16, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %16, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %16, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %16, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %16, %6;\n\t"
+      "madc.hi.u32    %7, %15, %16, %7;"
+      : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b));
+}
+
+// t[0..8] += lo(p[j] * m), p the field modulus as immediates.
+template <class F>
+__device__ __forceinline__ void row_lo_p(uint32_t t[9], uint32_t m) {
+  asm("mad.lo.cc.u32  %0, %9, %10, %0;\n\t"
+      "madc.lo.cc.u32 %1, %9, %11, %1;\n\t"
+      "madc.lo.cc.u32 %2, %9, %12, %2;\n\t"
+      "madc.lo.cc.u32 %3, %9, %13, %3;\n\t"
+      "madc.lo.cc.u32 %4, %9, %14, %4;\n\t"
+      "madc.lo.cc.u32 %5, %9, %15, %5;\n\t"
+      "madc.lo.cc.u32 %6, %9, %16, %6;\n\t"
+      "madc.lo.cc.u32 %7, %9, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;"
+      : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+        "+r"(t[8])
+      : "r"(m), "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
+        "n"(F::P7));
+}
+
+template <class F>
+__device__ __forceinline__ void row_hi_p(uint32_t t[9], uint32_t m) {
+  asm("mad.hi.cc.u32  %0, %8, %9,  %0;\n\t"
+      "madc.hi.cc.u32 %1, %8, %10, %1;\n\t"
+      "madc.hi.cc.u32 %2, %8, %11, %2;\n\t"
+      "madc.hi.cc.u32 %3, %8, %12, %3;\n\t"
+      "madc.hi.cc.u32 %4, %8, %13, %4;\n\t"
+      "madc.hi.cc.u32 %5, %8, %14, %5;\n\t"
+      "madc.hi.cc.u32 %6, %8, %15, %6;\n\t"
+      "madc.hi.u32    %7, %8, %16, %7;"
+      : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8])
+      : "r"(m), "n"(F::P0), "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6),
+        "n"(F::P7));
+}
+
+// r = t - p if t >= p else t   (t < 2p).
+template <class F>
+__device__ __forceinline__ void reduce_once(uint32_t r[8], const uint32_t t[8]) {
+  uint32_t d[8], bw;
+  const uint32_t zero = 0;
+  asm("sub.cc.u32  %0, %9,  %17;\n\t"
+      "subc.cc.u32 %1, %10, %18;\n\t"
+      "subc.cc.u32 %2, %11, %19;\n\t"
+      "subc.cc.u32 %3, %12, %20;\n\t"
+      "subc.cc.u32 %4, %13, %21;\n\t"
+      "subc.cc.u32 %5, %14, %22;\n\t"
+      "subc.cc.u32 %6, %15, %23;\n\t"
+      "subc.cc.u32 %7, %16, %24;\n\t"
+      "subc.u32    %8, %25, %25;"
+      : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+        "=r"(bw)
+      : "r"(t[0]), "r"(t[1]), "r"(t[2]), "r"(t[3]), "r"(t[4]), "r"(t[5]), "r"(t[6]), "r"(t[7]), "n"(F::P0),
+        "n"(F::P1), "n"(F::P2), "n"(F::P3), "n"(F::P4), "n"(F::P5), "n"(F::P6), "n"(F::P7), "r"(zero));
+  // bw = all ones when t < p (keep t), zero otherwise (take t - p).
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = (t[j] & bw) | (d[j] & ~bw);
+}
+
+// ---------------------------------------------------------------- field ops
+
+// r = a * b * 2^-256 mod p.  a, b canonical; r canonical.  r may alias a or b.
+template <class F>
+__device__ __forceinline__ void mont_mul(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+  uint32_t t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    row_lo(t, a, b[i]);
+    row_hi(t, a, b[i]);
+    const uint32_t m = t[0] * F::NP;
+    row_lo_p<F>(t, m);
+    row_hi_p<F>(t, m);
+    // t[0] is now zero: divide by 2^32.
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = t[j + 1];
+    t[8] = 0;
+  }
+  reduce_once<F>(r, t);
+}
+
+// r = a + b mod p.
+template <class F>
+__device__ __forceinline__ void add_mod(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+  uint32_t s[8];
+  asm("add.cc.u32  %0, %8,  %16;\n\t"
+      "addc.cc.u32 %1, %9,  %17;\n\t"
+      "addc.cc.u32 %2, %10, %18;\n\t"
+      "addc.cc.u32 %3, %11, %19;\n\t"
+      "addc.cc.u32 %4, %12, %20;\n\t"
+      "addc.cc.u32 %5, %13, %21;\n\t"
+      "addc.cc.u32 %6, %14, %22;\n\t"
+      "addc.u32    %7, %15, %23;"
+      : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]),
+        "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+  reduce_once<F>(r, s);
+}
+
+// r = a - b mod p.
+template <class F>
+__device__ __forceinline__ void sub_mod(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+  uint32_t d[8], bw;
+  const uint32_t zero = 0;
+  asm("sub.cc.u32  %0, %9,  %17;\n\t"
+      "subc.cc.u32 %1, %10, %18;\n\t"
+      "subc.cc.u32 %2, %11, %19;\n\t"
+      "subc.cc.u32 %3, %12, %20;\n\t"
+      "subc.cc.u32 %4, %13, %21;\n\t"
+      "subc.cc.u32 %5, %14, %22;\n\t"
+      "subc.cc.u32 %6, %15, %23;\n\t"
+      "subc.cc.u32 %7, %16, %24;\n\t"
+      "subc.u32    %8, %25, %25;"
+      : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+        "=r"(bw)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[0]),
+        "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(zero));
+  // add p back when the subtraction borrowed (bw = all ones)
+  asm("add.cc.u32  %0, %0, %8;\n\t"
+      "addc.cc.u32 %1, %1, %9;\n\t"
+      "addc.cc.u32 %2, %2, %10;\n\t"
+      "addc.cc.u32 %3, %3, %11;\n\t"
+      "addc.cc.u32 %4, %4, %12;\n\t"
+      "addc.cc.u32 %5, %5, %13;\n\t"
+      "addc.cc.u32 %6, %6, %14;\n\t"
+      "addc.u32    %7, %7, %15;"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7])
+      : "r"(F::P0 & bw), "r"(F::P1 & bw), "r"(F::P2 & bw), "r"(F::P3 & bw), "r"(F::P4 & bw),
+        "r"(F::P5 & bw), "r"(F::P6 & bw), "r"(F::P7 & bw));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = d[j];
+}
+
+__device__ __forceinline__ void fe_copy(uint32_t r[8], const uint32_t a[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = a[j];
+}
+
+// ------------------------------------------------------------- memory access
+
+// One element = 32 bytes = two 16-byte vectors.
+__device__ __forceinline__ void fe_load_global(uint32_t r[8], const uint4 *base, uint64_t elem) {
+  const uint4 lo = __ldg(base + 2 * elem);
+  const uint4 hi = __ldg(base + 2 * elem + 1);
+  r[0] = lo.x; r[1] = lo.y; r[2] = lo.z; r[3] = lo.w;
+  r[4] = hi.x; r[5] = hi.y; r[6] = hi.z; r[7] = hi.w;
+}
+
+// Plain (coherent) load: for buffers that an earlier kernel of the same
+// transform wrote.
+__device__ __forceinline__ void fe_load_global_rw(uint32_t r[8], const uint4 *base, uint64_t elem) {
+  const uint4 lo = base[2 * elem];
+  const uint4 hi = base[2 * elem + 1];
+  r[0] = lo.x; r[1] = lo.y; r[2] = lo.z; r[3] = lo.w;
+  r[4] = hi.x; r[5] = hi.y; r[6] = hi.z; r[7] = hi.w;
+}
+
+__device__ __forceinline__ void fe_store_global(uint4 *base, uint64_t elem, const uint32_t a[8]) {
+  base[2 * elem] = make_uint4(a[0], a[1], a[2], a[3]);
+  base[2 * elem + 1] = make_uint4(a[4], a[5], a[6], a[7]);
+}
+
+}  // namespace gb300ntt

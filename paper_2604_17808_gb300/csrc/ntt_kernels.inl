@@ -1,0 +1,144 @@
+// ntt_kernels.inl -- kernel instantiations and launchers for one field.
+// Included by kernels_bls12_381.cu and kernels_bn254.cu with NTT_FIELD set.
+#include "ntt_launch.h"
+
+namespace gb300ntt {
+namespace {
+
+using F = NTT_FIELD;
+
+__device__ __forceinline__ void fe_from_param(uint32_t r[8], const Fe32 &a) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = a.w[j];
+}
+
+// acc *= base^e using the ladder pw (bits of e below 32).
+__device__ __forceinline__ void ladder_mul(uint32_t acc[8], uint64_t e, const Pow2Table &pw) {
+  for (int b = 0; b < 32 && (e >> b) != 0; ++b) {
+    if ((e >> b) & 1) {
+      uint32_t w[8];
+      fe_from_param(w, pw.v[b]);
+      mont_mul<F>(acc, acc, w);
+    }
+  }
+}
+
+__global__ void gen_2d_kernel(uint4 *out, uint32_t log_s, uint32_t log_mp, const Pow2Table pw,
+                              const uint4 *fac, const Fe32 init) {
+  const uint64_t total = 1ull << (log_s + log_mp);
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t n = idx >> log_mp, q = idx & ((1ull << log_mp) - 1);
+    uint32_t acc[8];
+    fe_from_param(acc, init);
+    if (fac) {
+      uint32_t f[8];
+      fe_load_global(f, fac, n);
+      mont_mul<F>(acc, acc, f);
+    }
+    ladder_mul(acc, n * q, pw);
+    fe_store_global(out, idx, acc);
+  }
+}
+
+__global__ void gen_1d_kernel(uint4 *out, uint64_t count, const Pow2Table pw, const Fe32 init) {
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t acc[8];
+    fe_from_param(acc, init);
+    ladder_mul(acc, idx, pw);
+    fe_store_global(out, idx, acc);
+  }
+}
+
+__global__ void mul_vec_kernel(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count) {
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x[8], y[8];
+    fe_load_global(x, a, idx);
+    fe_load_global(y, b, idx);
+    mont_mul<F>(x, x, y);
+    fe_store_global(out, idx, x);
+  }
+}
+
+template <int LOGS, int MODE>
+cudaError_t set_pass_attr() {
+  return cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              pass_smem_bytes(LOGS));
+}
+
+template <int LOGS>
+cudaError_t set_pass_attrs() {
+  cudaError_t e = set_pass_attr<LOGS, kModeInner>();
+  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirst>();
+  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirstPre>();
+  return e;
+}
+
+cudaError_t prepare() {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = set_pass_attrs<1>();
+  if (e == cudaSuccess) e = set_pass_attrs<2>();
+  if (e == cudaSuccess) e = set_pass_attrs<3>();
+  if (e == cudaSuccess) e = set_pass_attrs<4>();
+  if (e == cudaSuccess) e = set_pass_attrs<5>();
+  if (e == cudaSuccess) e = set_pass_attrs<6>();
+  if (e == cudaSuccess) e = set_pass_attrs<7>();
+  if (e == cudaSuccess) e = set_pass_attrs<8>();
+  return e;
+}
+
+template <int LOGS>
+cudaError_t pass_logs(int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  const dim3 grid((unsigned)tiles), block(kPassThreads);
+  const int smem = pass_smem_bytes(LOGS);
+  switch (mode) {
+    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner><<<grid, block, smem, st>>>(a); break;
+    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst><<<grid, block, smem, st>>>(a); break;
+    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre><<<grid, block, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pass(int logs, int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  switch (logs) {
+    case 1: return pass_logs<1>(mode, a, tiles, st);
+    case 2: return pass_logs<2>(mode, a, tiles, st);
+    case 3: return pass_logs<3>(mode, a, tiles, st);
+    case 4: return pass_logs<4>(mode, a, tiles, st);
+    case 5: return pass_logs<5>(mode, a, tiles, st);
+    case 6: return pass_logs<6>(mode, a, tiles, st);
+    case 7: return pass_logs<7>(mode, a, tiles, st);
+    case 8: return pass_logs<8>(mode, a, tiles, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+unsigned grid_for(uint64_t count) {
+  uint64_t blocks = (count + 255) / 256;
+  if (blocks > 152ull * 64) blocks = 152ull * 64;
+  return (unsigned)(blocks ? blocks : 1);
+}
+
+cudaError_t gen_2d(uint4 *out, uint32_t log_s, uint32_t log_mp, const Pow2Table &pw, const uint4 *fac,
+                   Fe32 init, cudaStream_t st) {
+  gen_2d_kernel<<<grid_for(1ull << (log_s + log_mp)), 256, 0, st>>>(out, log_s, log_mp, pw, fac, init);
+  return cudaGetLastError();
+}
+
+cudaError_t gen_1d(uint4 *out, uint64_t count, const Pow2Table &pw, Fe32 init, cudaStream_t st) {
+  gen_1d_kernel<<<grid_for(count), 256, 0, st>>>(out, count, pw, init);
+  return cudaGetLastError();
+}
+
+cudaError_t mul_vec(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, cudaStream_t st) {
+  mul_vec_kernel<<<grid_for(count), 256, 0, st>>>(out, a, b, count);
+  return cudaGetLastError();
+}
+
+const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec};
+
+}  // namespace
+}  // namespace gb300ntt

@@ -1,0 +1,46 @@
+// ntt_launch.h -- host-side launchers of the per-field kernels.
+//
+// Each field's kernels are instantiated in its own translation unit
+// (kernels_bls12_381.cu, kernels_bn254.cu) so that the two compile in
+// parallel; the plan code dispatches on the field id.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ntt_pass.cuh"
+
+namespace gb300ntt {
+
+// One element as eight 32-bit limbs (kernel-argument form).
+struct Fe32 {
+  uint32_t w[8];
+};
+
+// base^(2^b) for b < 32, Montgomery form: the square-and-multiply ladder
+// used by the table generators.
+struct Pow2Table {
+  Fe32 v[32];
+};
+
+struct FieldLaunchers {
+  cudaError_t (*prepare)();
+  cudaError_t (*pass)(int logs, int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st);
+  // out[n * Mp + q] = init * fac[n] * base^(n*q)    (fac may be null)
+  cudaError_t (*gen_2d)(uint4 *out, uint32_t log_s, uint32_t log_mp, const Pow2Table &pw, const uint4 *fac,
+                        Fe32 init, cudaStream_t st);
+  // out[i] = init * base^i, i < count
+  cudaError_t (*gen_1d)(uint4 *out, uint64_t count, const Pow2Table &pw, Fe32 init, cudaStream_t st);
+  // out[i] = a[i] * b[i] * 2^-256 (element-wise Montgomery product; tests)
+  cudaError_t (*mul_vec)(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, cudaStream_t st);
+};
+
+const FieldLaunchers &launchers_bls12_381();
+const FieldLaunchers &launchers_bn254();
+
+inline const FieldLaunchers &launchers(int field) {
+  return field == 0 ? launchers_bls12_381() : launchers_bn254();
+}
+
+}  // namespace gb300ntt

@@ -1,0 +1,499 @@
+// ntt_plan.cu -- plans, resident twiddle tables and the C ABI.
+//
+// A plan fixes (field, log_n), splits N into passes of at most 2^8 points
+// (the four-step / six-step decomposition of ntt_pass.cuh), and builds on
+// the device every constant the passes multiply by, in Montgomery form:
+//   * per distinct pass size S: omega_S^i and omega_S^-i, i < S/2;
+//   * per pass j >= 1 and kind: the inter-pass table omega_M^(n q) [S_j][Mp]
+//     (inverse: omega^-1 and, in the last pass, N^-1; coset: times
+//     s^(n * N/M) for the digit the pass transforms);
+//   * pass 0 multipliers for coset (s^(n N/S_0)) and, for single-pass
+//     plans, the inverse scale N^-1.
+// The MORPH paper keeps its twiddle matrices resident ("generated offline",
+// Fig. 4); on GB300 they are generated once per plan by kernels and stay in
+// HBM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "../../include/ntt_gb300.h"
+#include "host_field.h"
+#include "ntt_launch.h"
+#include "ntt_plan.h"
+
+using namespace gb300ntt;
+
+namespace gb300ntt {
+
+namespace {
+
+Fe32 to_fe32(const U256 &a) {
+  Fe32 r;
+  for (int i = 0; i < 4; ++i) {
+    r.w[2 * i] = (uint32_t)a.w[i];
+    r.w[2 * i + 1] = (uint32_t)(a.w[i] >> 32);
+  }
+  return r;
+}
+
+U256 from_limbs(const uint64_t *l) { return U256{{l[0], l[1], l[2], l[3]}}; }
+
+Pow2Table make_ladder(const HostField &F, const U256 &base) {
+  Pow2Table t;
+  U256 b = base;
+  for (int i = 0; i < 32; ++i) {
+    t.v[i] = to_fe32(F.to_mont(b));
+    b = F.mul(b, b);
+  }
+  return t;
+}
+
+// omega^(2^k)
+U256 square_times(const HostField &F, U256 a, unsigned k) {
+  for (unsigned i = 0; i < k; ++i) a = F.mul(a, a);
+  return a;
+}
+
+std::mutex g_prep_mu;
+std::set<std::pair<int, int>> g_prepared;  // (device, field)
+
+ntt_status prepare_device(int device, int field) {
+  std::lock_guard<std::mutex> lk(g_prep_mu);
+  if (g_prepared.count({device, field})) return NTT_OK;
+  if (launchers(field).prepare() != cudaSuccess) return NTT_ERR_CUDA;
+  g_prepared.insert({device, field});
+  return NTT_OK;
+}
+
+ntt_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return NTT_OK;
+  if (e == cudaErrorMemoryAllocation) return NTT_ERR_OOM;
+  return NTT_ERR_CUDA;
+}
+
+}  // namespace
+
+// Split log_n into passes of at most kMaxPassLog bits, as equal as
+// possible, larger ones first.
+std::vector<uint32_t> split_passes(uint32_t log_n) {
+  const uint32_t P = (log_n + kMaxPassLog - 1) / kMaxPassLog;
+  std::vector<uint32_t> s(P, log_n / P);
+  for (uint32_t i = 0; i < log_n % P; ++i) s[i] += 1;
+  return s;
+}
+
+uint64_t pass_tiles(uint32_t log_n, uint32_t logs) {
+  const uint64_t num_sub = 1ull << (log_n - logs);
+  const uint64_t g = 1ull << (kTileLog - logs);
+  return (num_sub + g - 1) / g;
+}
+
+static ntt_status alloc_tab(ntt_plan p, uint4 **out, uint64_t elems) {
+  void *ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, elems * 32);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  p->allocations.push_back(ptr);
+  p->device_bytes += elems * 32;
+  *out = (uint4 *)ptr;
+  return NTT_OK;
+}
+
+#define NTT_TRY(expr)                  \
+  do {                                 \
+    ntt_status _s = (expr);            \
+    if (_s != NTT_OK) return _s;       \
+  } while (0)
+
+#define NTT_CUDA(expr) NTT_TRY(cuda_status(expr))
+
+// (Re)build the coset tables for shift s (standard form).
+ntt_status build_coset_tables(ntt_plan p, const U256 &s, cudaStream_t st) {
+  const HostField F = host_field(p->field);
+  const FieldLaunchers &L = launchers(p->field);
+  const uint32_t log_n = p->log_n, P = p->num_passes;
+  const Fe32 one = to_fe32(F.to_mont(u256(1)));
+  uint32_t log_m = 0;
+  for (uint32_t j = 0; j < P; ++j) {
+    const uint32_t logs = p->pass_log[j];
+    log_m += logs;
+    // s^(N/M_j): the coset factor of one step of digit j
+    const U256 step = F.pow(s, 1ull << (log_n - log_m));
+    if (j == 0) {
+      if (!p->pre[kCoset]) NTT_TRY(alloc_tab(p, &p->pre[kCoset], 1ull << logs));
+      NTT_CUDA(L.gen_1d(p->pre[kCoset], 1ull << logs, make_ladder(F, step), one, st));
+    } else {
+      if (!p->fac_coset[j]) NTT_TRY(alloc_tab(p, &p->fac_coset[j], 1ull << logs));
+      NTT_CUDA(L.gen_1d(p->fac_coset[j], 1ull << logs, make_ladder(F, step), one, st));
+      const uint32_t log_mp = log_m - logs;
+      const U256 w = square_times(F, p->omega, log_n - log_m);
+      if (!p->tw[kCoset][j]) NTT_TRY(alloc_tab(p, &p->tw[kCoset][j], 1ull << log_m));
+      NTT_CUDA(L.gen_2d(p->tw[kCoset][j], logs, log_mp, make_ladder(F, w), p->fac_coset[j], one, st));
+    }
+  }
+  p->coset_shift = s;
+  return NTT_OK;
+}
+
+ntt_status build_plan(ntt_plan p, cudaStream_t st) {
+  const HostField F = host_field(p->field);
+  const FieldLaunchers &L = launchers(p->field);
+  const uint32_t log_n = p->log_n;
+  const std::vector<uint32_t> passes = split_passes(log_n);
+  p->num_passes = (uint32_t)passes.size();
+  for (uint32_t j = 0; j < p->num_passes; ++j) p->pass_log[j] = passes[j];
+  const uint32_t P = p->num_passes;
+
+  p->omega = F.root_of_unity(log_n);
+  p->omega_inv = F.inv(p->omega);
+  const U256 n_inv = F.inv(F.reduce_small(1ull << log_n));
+  const Fe32 one = to_fe32(F.to_mont(u256(1)));
+  const Fe32 n_inv_m = to_fe32(F.to_mont(n_inv));
+
+  // DFT twiddles per distinct pass size
+  for (uint32_t j = 0; j < P; ++j) {
+    const uint32_t logs = passes[j];
+    for (int dir = 0; dir < 2; ++dir) {
+      if (p->dft_tw[dir][logs]) continue;
+      const U256 w = square_times(F, dir ? p->omega_inv : p->omega, log_n - logs);
+      const uint64_t count = std::max<uint64_t>(1, (1ull << logs) / 2);
+      NTT_TRY(alloc_tab(p, &p->dft_tw[dir][logs], count));
+      NTT_CUDA(L.gen_1d(p->dft_tw[dir][logs], count, make_ladder(F, w), one, st));
+    }
+  }
+  // inter-pass tables (forward, inverse)
+  uint32_t log_m = passes[0];
+  for (uint32_t j = 1; j < P; ++j) {
+    const uint32_t logs = passes[j];
+    const uint32_t log_mp = log_m;
+    log_m += logs;
+    for (int dir = 0; dir < 2; ++dir) {
+      const U256 w = square_times(F, dir ? p->omega_inv : p->omega, log_n - log_m);
+      const Fe32 init = (dir == 1 && j == P - 1) ? n_inv_m : one;
+      NTT_TRY(alloc_tab(p, &p->tw[dir][j], 1ull << log_m));
+      NTT_CUDA(L.gen_2d(p->tw[dir][j], logs, log_mp, make_ladder(F, w), nullptr, init, st));
+    }
+  }
+  // single-pass inverse: N^-1 as a pass-0 multiplier
+  if (P == 1) {
+    NTT_TRY(alloc_tab(p, &p->pre[kInverse], 1ull << passes[0]));
+    NTT_CUDA(L.gen_1d(p->pre[kInverse], 1ull << passes[0], make_ladder(F, u256(1)), n_inv_m, st));
+  }
+  if (p->has_coset) NTT_TRY(build_coset_tables(p, F.reduce_small(F.generator), st));
+  if (P > 1) NTT_TRY(alloc_tab(p, &p->scratch, 1ull << log_n));
+  p->launches = P;
+  return NTT_OK;
+}
+
+// Enqueue one transform.  Exposed to the batched path as well.
+ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st) {
+  const FieldLaunchers &L = launchers(p->field);
+  const uint32_t P = p->num_passes, log_n = p->log_n;
+  const int dir = kind == kInverse ? 1 : 0;
+  uint4 *work = (P > 1 && in == out) ? p->scratch : (uint4 *)out;
+  for (uint32_t j = 0; j < P; ++j) {
+    const uint32_t logs = p->pass_log[j];
+    PassArgs a{};
+    a.dft_tw = p->dft_tw[dir][logs];
+    a.num_sub = 1ull << (log_n - logs);
+    int mode;
+    if (j == 0) {
+      a.src = (const uint4 *)in;
+      a.dst = P == 1 ? (uint4 *)out : work;
+      a.log_mp = log_n - logs;
+      a.num_digits = P - 1;
+      uint32_t shift = 0;
+      for (uint32_t d = 1; d < P; ++d) {
+        a.digit_log[d - 1] = p->pass_log[d];
+        a.digit_shift[d - 1] = shift;
+        shift += p->pass_log[d];
+      }
+      a.mul = p->pre[kind];
+      mode = a.mul ? kModeFirstPre : kModeFirst;
+    } else {
+      uint32_t log_mp = 0;
+      for (uint32_t i = 0; i < j; ++i) log_mp += p->pass_log[i];
+      a.src = work;
+      a.dst = j == P - 1 ? (uint4 *)out : work;
+      a.log_mp = log_mp;
+      a.mul = p->tw[kind][j];
+      mode = kModeInner;
+    }
+    cudaError_t e = timing_begin(p, (int)j, st);
+    if (e == cudaSuccess) e = L.pass((int)logs, mode, a, pass_tiles(log_n, logs), st);
+    if (e == cudaSuccess) e = timing_end(p, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return NTT_OK;
+}
+
+static cudaEvent_t next_event(ntt_plan p) {
+  if (p->ev_next == p->ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p->ev_pool.push_back(e);
+  }
+  return p->ev_pool[p->ev_next++];
+}
+
+cudaError_t timing_begin(ntt_plan p, int pass, cudaStream_t st) {
+  if (!p->timing) return cudaSuccess;
+  cudaEvent_t a = next_event(p), b = next_event(p);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  p->ev_used.push_back({pass, {a, b}});
+  return cudaEventRecord(a, st);
+}
+
+cudaError_t timing_end(ntt_plan p, cudaStream_t st) {
+  if (!p->timing) return cudaSuccess;
+  return cudaEventRecord(p->ev_used.back().second.second, st);
+}
+
+ntt_status check_buffer(const void *ptr) {
+  if (!ptr) return NTT_ERR_INVALID_ARG;
+  if ((uintptr_t)ptr % 16) return NTT_ERR_INVALID_ARG;
+  return NTT_OK;
+}
+
+}  // namespace gb300ntt
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int coset) {
+  if (!out) return NTT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (field != NTT_FIELD_BLS12_381_FR && field != NTT_FIELD_BN254_FR) return NTT_ERR_INVALID_ARG;
+  const uint32_t adicity = field == NTT_FIELD_BLS12_381_FR ? 32 : 28;
+  if (log_n < 1 || log_n > adicity || log_n > 28) return NTT_ERR_UNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return NTT_ERR_NO_DEVICE;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return NTT_ERR_NO_DEVICE;
+  }
+  if (prop.major != 10 || prop.minor != 3) return NTT_ERR_NO_DEVICE;
+  NTT_TRY(prepare_device(dev, (int)field));
+  ntt_plan p = new (std::nothrow) ntt_plan_s();
+  if (!p) return NTT_ERR_OOM;
+  p->device = dev;
+  p->field = (int)field;
+  p->log_n = log_n;
+  p->has_coset = coset != 0;
+  p->path = NTT_PATH_AUTO;
+  p->sm_count = prop.multiProcessorCount;
+  cudaStream_t st = nullptr;
+  ntt_status s = cuda_status(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  if (s == NTT_OK) s = build_plan(p, st);
+  if (st) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (s == NTT_OK) s = cuda_status(e);
+    cudaStreamDestroy(st);
+  }
+  if (s == NTT_OK) s = cuda_status(cudaMalloc(&p->d_err, sizeof(uint32_t)));
+  if (s == NTT_OK) s = cuda_status(cudaMemset(p->d_err, 0, sizeof(uint32_t)));
+  if (s != NTT_OK) {
+    ntt_plan_destroy(p);
+    return s;
+  }
+  *out = p;
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_set_path(ntt_plan plan, ntt_path path) {
+  if (!plan) return NTT_ERR_INVALID_ARG;
+  if (path != NTT_PATH_AUTO && path != NTT_PATH_BUTTERFLY && path != NTT_PATH_MATRIX) return NTT_ERR_INVALID_ARG;
+  if (path == NTT_PATH_MATRIX && !matrix_path_available(plan)) return NTT_ERR_UNSUPPORTED;
+  plan->path = path;
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_set_coset_shift(ntt_plan plan, const uint64_t shift[4]) {
+  if (!plan || !shift) return NTT_ERR_INVALID_ARG;
+  if (!plan->has_coset) return NTT_ERR_INVALID_ARG;
+  const HostField F = host_field(plan->field);
+  const U256 s = from_limbs(shift);
+  if (u256_geq(s, F.p) || u256_is_zero(s)) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = nullptr;
+  NTT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  ntt_status r = build_coset_tables(plan, s, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (r == NTT_OK) r = cuda_status(e);
+  return r;
+}
+
+ntt_status ntt_plan_destroy(ntt_plan plan) {
+  if (!plan) return NTT_OK;
+  cudaDeviceSynchronize();
+  for (void *ptr : plan->allocations) cudaFree(ptr);
+  if (plan->d_err) cudaFree(plan->d_err);
+  for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
+  release_matrix_resources(plan);
+  delete plan;
+  return NTT_OK;
+}
+
+ntt_status ntt_execute(ntt_plan plan, ntt_kind kind, const void *d_in, void *d_out, ntt_stream stream) {
+  if (!plan) return NTT_ERR_INVALID_ARG;
+  if (kind != NTT_KIND_FORWARD && kind != NTT_KIND_INVERSE && kind != NTT_KIND_COSET) return NTT_ERR_INVALID_ARG;
+  if (kind == NTT_KIND_COSET && !plan->has_coset) return NTT_ERR_INVALID_ARG;
+  NTT_TRY(check_buffer(d_in));
+  NTT_TRY(check_buffer(d_out));
+  if (plan->path == NTT_PATH_MATRIX) return enqueue_matrix_transform(plan, (int)kind, d_in, d_out, (cudaStream_t)stream);
+  return enqueue_transform(plan, (int)kind, d_in, d_out, (cudaStream_t)stream);
+}
+
+ntt_status ntt_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream) {
+  return ntt_execute(plan, NTT_KIND_FORWARD, d_in, d_out, stream);
+}
+ntt_status ntt_inverse(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream) {
+  return ntt_execute(plan, NTT_KIND_INVERSE, d_in, d_out, stream);
+}
+ntt_status ntt_coset_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream) {
+  return ntt_execute(plan, NTT_KIND_COSET, d_in, d_out, stream);
+}
+
+ntt_status ntt_transform_host(ntt_plan plan, ntt_kind kind, const void *h_in, void *h_out, void *d_work,
+                              ntt_stream stream) {
+  if (!plan || !h_in || !h_out) return NTT_ERR_INVALID_ARG;
+  NTT_TRY(check_buffer(d_work));
+  const size_t bytes = (size_t)32 << plan->log_n;
+  cudaStream_t st = (cudaStream_t)stream;
+  NTT_CUDA(cudaMemcpyAsync(d_work, h_in, bytes, cudaMemcpyHostToDevice, st));
+  NTT_TRY(ntt_execute(plan, kind, d_work, d_work, stream));
+  NTT_CUDA(cudaMemcpyAsync(h_out, d_work, bytes, cudaMemcpyDeviceToHost, st));
+  NTT_CUDA(cudaStreamSynchronize(st));
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out) {
+  if (!plan || !out) return NTT_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof *out);
+  out->field = (uint32_t)plan->field;
+  out->log_n = plan->log_n;
+  out->num_passes = plan->num_passes;
+  for (uint32_t j = 0; j < plan->num_passes && j < 4; ++j) out->pass_log[j] = plan->pass_log[j];
+  out->launches_per_transform = plan->path == NTT_PATH_MATRIX ? matrix_launches(plan) : plan->launches;
+  out->path = (uint32_t)plan->path;
+  out->device_bytes = plan->device_bytes;
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_read_table(ntt_plan plan, ntt_kind kind, uint32_t pass, uint32_t table, uint64_t first,
+                               uint64_t count, void *h_out) {
+  if (!plan || !h_out) return NTT_ERR_INVALID_ARG;
+  if (kind != NTT_KIND_FORWARD && kind != NTT_KIND_INVERSE && kind != NTT_KIND_COSET) return NTT_ERR_INVALID_ARG;
+  if (pass >= plan->num_passes) return NTT_ERR_INVALID_ARG;
+  const uint32_t logs = plan->pass_log[pass];
+  const uint4 *src = nullptr;
+  uint64_t size = 0;
+  if (table == 0) {
+    src = plan->dft_tw[kind == NTT_KIND_INVERSE ? 1 : 0][logs];
+    size = std::max<uint64_t>(1, (1ull << logs) / 2);
+  } else if (table == 1) {
+    if (pass == 0) {
+      src = plan->pre[kind];
+      size = 1ull << logs;
+    } else {
+      src = plan->tw[kind][pass];
+      uint32_t log_m = 0;
+      for (uint32_t i = 0; i <= pass; ++i) log_m += plan->pass_log[i];
+      size = 1ull << log_m;
+    }
+  } else {
+    return NTT_ERR_INVALID_ARG;
+  }
+  if (!src || first > size || count > size - first) return NTT_ERR_INVALID_ARG;
+  std::vector<uint64_t> buf(count * 4);
+  NTT_CUDA(cudaMemcpy(buf.data(), src + 2 * first, count * 32, cudaMemcpyDeviceToHost));
+  const HostField F = host_field(plan->field);
+  const U256 rinv = F.r_inv();
+  uint64_t *o = (uint64_t *)h_out;
+  for (uint64_t i = 0; i < count; ++i) {
+    const U256 v = F.mul(from_limbs(&buf[4 * i]), rinv);
+    std::memcpy(o + 4 * i, v.w, 32);
+  }
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_enable_timing(ntt_plan plan, int enable) {
+  if (!plan) return NTT_ERR_INVALID_ARG;
+  plan->timing = enable != 0;
+  return NTT_OK;
+}
+
+ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[4], uint64_t launches_per_pass[4]) {
+  if (!plan || !ms_per_pass || !launches_per_pass) return NTT_ERR_INVALID_ARG;
+  for (int j = 0; j < 4; ++j) {
+    ms_per_pass[j] = 0;
+    launches_per_pass[j] = 0;
+  }
+  ntt_status s = NTT_OK;
+  for (auto &u : plan->ev_used) {
+    float ms = 0;
+    const cudaError_t e = cudaEventSynchronize(u.second.second);
+    if (e == cudaSuccess && cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess) {
+      if (u.first >= 0 && u.first < 4) {
+        ms_per_pass[u.first] += ms;
+        launches_per_pass[u.first] += 1;
+      }
+    } else {
+      s = NTT_ERR_CUDA;
+    }
+  }
+  plan->ev_used.clear();
+  plan->ev_next = 0;
+  return s;
+}
+
+ntt_status ntt_plan_poll_error(ntt_plan plan, uint32_t *code) {
+  if (!plan || !code) return NTT_ERR_INVALID_ARG;
+  NTT_CUDA(cudaDeviceSynchronize());
+  NTT_CUDA(cudaMemcpy(code, plan->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  NTT_CUDA(cudaMemset(plan->d_err, 0, sizeof(uint32_t)));
+  return NTT_OK;
+}
+
+ntt_status ntt_field_mont_mul(ntt_field field, const void *d_a, const void *d_b, void *d_out, uint64_t count,
+                              ntt_stream stream) {
+  if (field != NTT_FIELD_BLS12_381_FR && field != NTT_FIELD_BN254_FR) return NTT_ERR_INVALID_ARG;
+  if (count == 0) return NTT_OK;
+  NTT_TRY(check_buffer(d_a));
+  NTT_TRY(check_buffer(d_b));
+  NTT_TRY(check_buffer(d_out));
+  return cuda_status(
+      launchers((int)field).mul_vec((uint4 *)d_out, (const uint4 *)d_a, (const uint4 *)d_b, count, (cudaStream_t)stream));
+}
+
+const char *ntt_status_string(ntt_status status) {
+  switch (status) {
+    case NTT_OK: return "NTT_OK";
+    case NTT_ERR_INVALID_ARG: return "NTT_ERR_INVALID_ARG";
+    case NTT_ERR_UNSUPPORTED: return "NTT_ERR_UNSUPPORTED";
+    case NTT_ERR_OOM: return "NTT_ERR_OOM";
+    case NTT_ERR_CUDA: return "NTT_ERR_CUDA";
+    case NTT_ERR_TIMEOUT: return "NTT_ERR_TIMEOUT";
+    case NTT_ERR_BUDGET: return "NTT_ERR_BUDGET";
+    case NTT_ERR_NO_DEVICE: return "NTT_ERR_NO_DEVICE";
+  }
+  return "NTT_ERR_UNKNOWN";
+}
+
+uint32_t ntt_version(void) { return 100; }
+
+}  // extern "C"

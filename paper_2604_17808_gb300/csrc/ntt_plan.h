@@ -1,0 +1,65 @@
+// ntt_plan.h -- the plan object behind the C ABI's opaque ntt_plan.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "../../include/ntt_gb300.h"
+#include "host_field.h"
+
+namespace gb300ntt {
+
+enum Kind : int { kForward = 0, kInverse = 1, kCoset = 2 };
+
+struct MatrixResources;  // tensor-core path (ntt_matrix.cu)
+
+}  // namespace gb300ntt
+
+struct ntt_plan_s {
+  int device = 0;
+  int field = 0;
+  uint32_t log_n = 0;
+  bool has_coset = false;
+  ntt_path path = NTT_PATH_AUTO;
+  int sm_count = 0;
+  uint32_t num_passes = 0;
+  uint32_t pass_log[4] = {0, 0, 0, 0};
+  uint32_t launches = 0;
+  gb300ntt::U256 omega{}, omega_inv{}, coset_shift{};
+  // device tables, Montgomery form, 32 bytes per entry
+  uint4 *dft_tw[2][9] = {};      // [direction][log S]: omega_S^(+-i), i < S/2
+  uint4 *tw[3][4] = {};          // [kind][pass >= 1]: inter-pass multipliers [S_j][Mp]
+  uint4 *pre[3] = {};            // [kind]: pass-0 multipliers [S_0] (coset; single-pass inverse)
+  uint4 *fac_coset[4] = {};      // [pass >= 1]: s^(n N / M_j), n < S_j
+  uint4 *scratch = nullptr;      // N elements (in-place transforms with > 1 pass)
+  uint32_t *d_err = nullptr;     // device error word
+  std::vector<void *> allocations;
+  uint64_t device_bytes = 0;
+  gb300ntt::MatrixResources *matrix = nullptr;
+  // per-pass launch timing (ntt_plan_enable_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;             // all events created for timing
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (pass, start/stop)
+  size_t ev_next = 0;
+};
+
+namespace gb300ntt {
+
+std::vector<uint32_t> split_passes(uint32_t log_n);
+uint64_t pass_tiles(uint32_t log_n, uint32_t logs);
+ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
+ntt_status check_buffer(const void *ptr);
+// Timing hooks around one launch of pass `pass` (no-ops unless timing is on).
+cudaError_t timing_begin(ntt_plan p, int pass, cudaStream_t st);
+cudaError_t timing_end(ntt_plan p, cudaStream_t st);
+
+// matrix (tensor-core) path, ntt_matrix.cu
+bool matrix_path_available(ntt_plan p);
+ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
+uint32_t matrix_launches(ntt_plan p);
+void release_matrix_resources(ntt_plan p);
+
+}  // namespace gb300ntt

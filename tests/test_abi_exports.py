@@ -1,0 +1,66 @@
+"""The C-ABI library loads and exports every function include/ntt_gb300.h
+declares; argument checks that need no GPU behave as documented."""
+
+from __future__ import annotations
+
+import ctypes
+
+import pytest
+
+from paper_2604_17808_gb300 import _build, _native
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _native.load()
+
+
+def test_header_declares_the_boundary():
+    names = _native.declared_functions()
+    for required in ("ntt_plan_create", "ntt_plan_set_path", "ntt_plan_set_coset_shift", "ntt_plan_destroy",
+                     "ntt_forward", "ntt_inverse", "ntt_coset_forward", "ntt_batch_submit", "ntt_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _native.declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in the header but not exported"
+        assert name in _native._SIGS, f"{name} has no Python binding"
+
+
+def test_status_strings_and_version(lib):
+    for code, name in _native.STATUS_NAMES.items():
+        assert _native.ntt_status_string(code) == name
+    assert _native.ntt_status_string(99) == "NTT_ERR_UNKNOWN"
+    assert _native.ntt_version() >= 100
+
+
+def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.ntt_plan_create(None, 0, 12, 0) == 1
+    assert lib.ntt_plan_create(ctypes.byref(h), 5, 12, 0) == 1
+    assert lib.ntt_plan_create(ctypes.byref(h), 0, 0, 0) == 2
+    assert lib.ntt_plan_create(ctypes.byref(h), 0, 29, 0) == 2
+    assert lib.ntt_plan_create(ctypes.byref(h), 1, 29, 0) == 2  # BN254 2-adicity is 28
+    assert h.value is None
+
+
+def test_null_plan_calls_are_rejected(lib):
+    assert lib.ntt_forward(None, None, None, None) == 1
+    assert lib.ntt_execute(None, 0, None, None, None) == 1
+    assert lib.ntt_plan_destroy(None) == 0
+    assert lib.ntt_batch_submit(None, 0, None) == 0
+    assert lib.ntt_field_mont_mul(3, None, None, None, 1, None) == 1
+
+
+def test_no_gpu_is_reported_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.ntt_plan_create(ctypes.byref(h), 0, 12, 0) == 7  # NTT_ERR_NO_DEVICE
+    with pytest.raises(_native.NttError):
+        _native.ntt_plan_create("bls12_381_fr", 12)
