@@ -30,7 +30,7 @@
  * legacy default stream) and return without synchronising.  Their status
  * covers argument and launch errors only.  Errors detected on the device
  * (a bounded wait that ran out, see ntt_batch_submit) are read afterwards
- * with ntt_plan_poll_error / ntt_batch_poll_error.
+ * with ntt_batch_poll_error.
  *
  * Concurrency: a plan is immutable after creation (except the two setters
  * below, which must not race with transforms).  Out-of-place transforms
@@ -163,11 +163,27 @@ ntt_status ntt_plan_read_table(ntt_plan plan, ntt_kind kind, uint32_t pass, uint
                                uint64_t first, uint64_t count, void *h_out);
 
 /*
- * Batched submission: many independent transforms of possibly different
- * sizes and fields in one persistent kernel launch.  jobs[i].plan fixes field
- * and size; kind is an ntt_kind; in/out are device buffers as above (in-place
- * jobs are rejected with NTT_ERR_INVALID_ARG: the batched path has no
- * scratch).  Stream-ordered.
+ * Batched submission (the paper batches NTTs to fill its matrix units,
+ * Sec. 4.4 / Fig. 7): many independent transforms of possibly different
+ * sizes, kinds and fields, run as one persistent kernel launch per field in
+ * which the CTAs pull (job, pass, tile) work items from a device queue.
+ * jobs[i].plan fixes field and size; kind is an ntt_kind; in/out are device
+ * buffers as above.  Jobs must not overlap in memory, and in != out for every
+ * job (in-place jobs are rejected with NTT_ERR_INVALID_ARG: the batched path
+ * works in the output buffer).  Plans on the matrix path are rejected with
+ * NTT_ERR_UNSUPPORTED.
+ *
+ * The first submission of a given job list (same plans, kinds and pointers)
+ * builds its work-item table on the device and captures the launch sequence
+ * into a CUDA graph (synchronous, a few hundred microseconds); later
+ * submissions of the same list replay the graph (asynchronous).  Up to 16
+ * job lists are cached; destroying a plan drops the lists that use it.
+ * Submissions of one job list must not overlap in time (they share the
+ * list's device counters): order them on one stream.
+ *
+ * Every device-side wait of a batch is bounded (ntt_batch_set_wait_limit,
+ * default 2 s); when one runs out the kernel stops and records
+ * NTT_ERR_TIMEOUT, which ntt_batch_poll_error reports.
  */
 typedef struct ntt_job {
     ntt_plan plan;
@@ -176,6 +192,23 @@ typedef struct ntt_job {
     void *out;
 } ntt_job;
 ntt_status ntt_batch_submit(const ntt_job *jobs, size_t n, ntt_stream stream);
+
+/* First error recorded by batched kernels on the current device since the
+ * last poll (0 = none), then cleared.  Synchronises the device. */
+ntt_status ntt_batch_poll_error(uint32_t *code);
+
+/* Bound of every device-side wait of batches built from now on (ns, > 0).
+ * Drops the cached job lists. */
+ntt_status ntt_batch_set_wait_limit(uint64_t ns);
+
+/* Test hook (fault injection on the host): when enabled, every job list
+ * built from now on makes one of its device waits unsatisfiable, so that
+ * the bounded-wait path runs out and reports NTT_ERR_TIMEOUT.  No GPU fault
+ * is involved.  Drops the cached job lists. */
+ntt_status ntt_batch_debug_stall(int enable);
+
+/* Drop every cached job list (synchronises the device). */
+ntt_status ntt_batch_cache_clear(void);
 
 /*
  * Per-pass launch timing.  While enabled, every pass launch of this plan's

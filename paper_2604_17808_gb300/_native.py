@@ -65,6 +65,10 @@ _SIGS = {
     "ntt_plan_read_table": (ctypes.c_int, [_VP, ctypes.c_int, _U32, _U32, _U64, _U64, _VP]),
     "ntt_batch_submit": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP]),
     "ntt_plan_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
+    "ntt_batch_poll_error": (ctypes.c_int, [ctypes.POINTER(_U32)]),
+    "ntt_batch_set_wait_limit": (ctypes.c_int, [_U64]),
+    "ntt_batch_debug_stall": (ctypes.c_int, [ctypes.c_int]),
+    "ntt_batch_cache_clear": (ctypes.c_int, []),
     "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
     "ntt_plan_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ntt_plan_read_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U64)]),
@@ -199,6 +203,24 @@ def ntt_batch_submit(jobs, stream=None) -> None:
     for i, (plan, kind, d_in, d_out) in enumerate(jobs):
         arr[i] = Job(plan, _kind(kind), _ptr(d_in), _ptr(d_out))
     _check(load().ntt_batch_submit(arr, len(jobs), _stream(stream)), "ntt_batch_submit")
+
+
+def ntt_batch_poll_error() -> int:
+    code = _U32()
+    _check(load().ntt_batch_poll_error(ctypes.byref(code)), "ntt_batch_poll_error")
+    return int(code.value)
+
+
+def ntt_batch_set_wait_limit(ns: int) -> None:
+    _check(load().ntt_batch_set_wait_limit(int(ns)), "ntt_batch_set_wait_limit")
+
+
+def ntt_batch_debug_stall(enable: bool) -> None:
+    _check(load().ntt_batch_debug_stall(1 if enable else 0), "ntt_batch_debug_stall")
+
+
+def ntt_batch_cache_clear() -> None:
+    _check(load().ntt_batch_cache_clear(), "ntt_batch_cache_clear")
 
 
 def ntt_plan_poll_error(plan: int) -> int:

@@ -1,5 +1,6 @@
 // ntt_kernels.inl -- kernel instantiations and launchers for one field.
 // Included by kernels_bls12_381.cu and kernels_bn254.cu with NTT_FIELD set.
+#include "../../include/ntt_gb300.h"
 #include "ntt_launch.h"
 
 namespace gb300ntt {
@@ -62,6 +63,106 @@ __global__ void mul_vec_kernel(uint4 *out, const uint4 *a, const uint4 *b, uint6
   }
 }
 
+// ------------------------------------------------- persistent batch kernel
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int LOGS>
+__device__ __forceinline__ void batch_tile_logs(const BatchSeg &sg, uint64_t tile, uint4 *smem) {
+  switch (sg.mode) {
+    case kModeInner: pass_tile<F, LOGS, kModeInner, true>(sg.a, tile, smem); break;
+    case kModeFirst: pass_tile<F, LOGS, kModeFirst, true>(sg.a, tile, smem); break;
+    default: pass_tile<F, LOGS, kModeFirstPre, true>(sg.a, tile, smem); break;
+  }
+}
+
+__device__ __forceinline__ void batch_tile(const BatchSeg &sg, uint64_t tile, uint4 *smem) {
+  switch (sg.logs) {
+    case 1: batch_tile_logs<1>(sg, tile, smem); break;
+    case 2: batch_tile_logs<2>(sg, tile, smem); break;
+    case 3: batch_tile_logs<3>(sg, tile, smem); break;
+    case 4: batch_tile_logs<4>(sg, tile, smem); break;
+    case 5: batch_tile_logs<5>(sg, tile, smem); break;
+    case 6: batch_tile_logs<6>(sg, tile, smem); break;
+    case 7: batch_tile_logs<7>(sg, tile, smem); break;
+    case 8: batch_tile_logs<8>(sg, tile, smem); break;
+    case 9: batch_tile_logs<9>(sg, tile, smem); break;
+    case 10: batch_tile_logs<10>(sg, tile, smem); break;
+    default: batch_tile_logs<11>(sg, tile, smem); break;
+  }
+}
+
+// CTAs claim items (one tile of one pass of one job) in increasing order.
+// An item of pass j waits until every tile of pass j-1 of its job is done;
+// those tiles have smaller item indices, so they are held by CTAs that have
+// already started and never wait on later items: no deadlock.  Every wait
+// is bounded by b.wait_ns (globaltimer); on timeout the CTA records
+// NTT_ERR_TIMEOUT in *b.err and returns, and every CTA stops claiming
+// items once *b.err is set.
+__global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) batch_kernel(const BatchLaunch b) {
+  extern __shared__ uint4 smem[];
+  __shared__ uint32_t s_item;
+  __shared__ int32_t s_seg;
+  __shared__ int s_abort;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      uint32_t item = atomicAdd(b.head, 1u);
+      if (*(volatile uint32_t *)b.err != 0) item = b.total_items;
+      int32_t seg = -1;
+      int abort = 0;
+      if (item < b.total_items) {
+        int lo = 0, hi = (int)b.num_segs - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (b.segs[mid].first_item <= item) lo = mid;
+          else hi = mid - 1;
+        }
+        seg = lo;
+        const int32_t dep = b.segs[lo].dep_seg;
+        if (dep >= 0) {
+          const uint32_t need = b.segs[lo].dep_tiles;
+          const uint64_t t0 = global_ns();
+          while (ld_acquire_gpu(b.done + dep) < need) {
+            if (global_ns() - t0 > b.wait_ns) {
+              atomicCAS(b.err, 0u, (uint32_t)NTT_ERR_TIMEOUT);
+              abort = 1;
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+      }
+      s_item = item;
+      s_seg = seg;
+      s_abort = abort;
+    }
+    __syncthreads();
+    if (s_item >= b.total_items || s_abort) return;
+    const BatchSeg &sg = b.segs[s_seg];
+    batch_tile(sg, s_item - sg.first_item, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(b.done + s_seg, 1u);
+    }
+  }
+}
+
+cudaError_t batch(const BatchLaunch &b, cudaStream_t st) {
+  batch_kernel<<<b.grid, kPassThreads, kTileBytes, st>>>(b);
+  return cudaGetLastError();
+}
+
 template <int LOGS, int MODE>
 cudaError_t set_pass_attr() {
   return cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -86,6 +187,11 @@ cudaError_t prepare() {
   if (e == cudaSuccess) e = set_pass_attrs<6>();
   if (e == cudaSuccess) e = set_pass_attrs<7>();
   if (e == cudaSuccess) e = set_pass_attrs<8>();
+  if (e == cudaSuccess) e = set_pass_attrs<9>();
+  if (e == cudaSuccess) e = set_pass_attrs<10>();
+  if (e == cudaSuccess) e = set_pass_attrs<11>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
   return e;
 }
 
@@ -112,6 +218,9 @@ cudaError_t pass(int logs, int mode, const PassArgs &a, uint64_t tiles, cudaStre
     case 6: return pass_logs<6>(mode, a, tiles, st);
     case 7: return pass_logs<7>(mode, a, tiles, st);
     case 8: return pass_logs<8>(mode, a, tiles, st);
+    case 9: return pass_logs<9>(mode, a, tiles, st);
+    case 10: return pass_logs<10>(mode, a, tiles, st);
+    case 11: return pass_logs<11>(mode, a, tiles, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -138,7 +247,7 @@ cudaError_t mul_vec(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, 
   return cudaGetLastError();
 }
 
-const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec};
+const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec, batch};
 
 }  // namespace
 }  // namespace gb300ntt

@@ -24,6 +24,30 @@ struct Pow2Table {
   Fe32 v[32];
 };
 
+// One segment of a batched launch: all tiles of one pass of one job.
+// Segments are ordered by pass level, so a segment only ever depends on an
+// earlier one (deadlock-free with any number of resident CTAs).
+struct BatchSeg {
+  PassArgs a;
+  uint32_t logs;        // log2 of the pass's sub-transform size
+  uint32_t mode;        // PassMode
+  uint32_t first_item;  // index of the segment's first tile in the item space
+  uint32_t num_tiles;
+  int32_t dep_seg;      // segment that must be complete first, or -1
+  uint32_t dep_tiles;   // number of tiles of dep_seg
+};
+
+struct BatchLaunch {
+  const BatchSeg *segs;   // device array, sorted by first_item
+  uint32_t num_segs;
+  uint32_t total_items;
+  uint32_t *head;         // device: next item to claim (zeroed before launch)
+  uint32_t *done;         // device: completed tiles per segment (zeroed)
+  uint32_t *err;          // device: first error code (NTT_ERR_TIMEOUT)
+  uint64_t wait_ns;       // bound of every dependency wait
+  uint32_t grid;          // CTAs (a multiple of the SM count)
+};
+
 struct FieldLaunchers {
   cudaError_t (*prepare)();
   cudaError_t (*pass)(int logs, int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st);
@@ -34,6 +58,8 @@ struct FieldLaunchers {
   cudaError_t (*gen_1d)(uint4 *out, uint64_t count, const Pow2Table &pw, Fe32 init, cudaStream_t st);
   // out[i] = a[i] * b[i] * 2^-256 (element-wise Montgomery product; tests)
   cudaError_t (*mul_vec)(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, cudaStream_t st);
+  // persistent batched kernel over the items of `b`
+  cudaError_t (*batch)(const BatchLaunch &b, cudaStream_t st);
 };
 
 const FieldLaunchers &launchers_bls12_381();

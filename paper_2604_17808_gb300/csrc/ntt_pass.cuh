@@ -20,22 +20,28 @@
 // After the last pass the buffer holds X in natural order.  Coset and
 // inverse scale factors are folded into the same per-element multipliers.
 //
-// Work split on the GPU: one CTA (256 threads, 8 warps) owns a tile of
-// 2048 elements = G = 2048/S sub-transforms with consecutive sub-transform
-// index, staged in shared memory.
+// Work split on the GPU: one CTA (256 threads) owns a tile of 2048 elements
+// (64 KiB of shared memory) = G = 2048/S sub-transforms with consecutive
+// sub-transform index.
 //   load phase : consecutive threads read consecutive 32-byte elements
 //                (coalesced), multiply by the input multiplier (pass >= 1:
 //                omega_M^(n q), read with the same coalesced pattern), and
 //                write the tile;
-//   warp phase : warp w transforms tile elements [256w, 256w+256) -- one
-//                sub-transform of 256 points or 256/S smaller ones -- as a
-//                decimation-in-frequency (Gentleman-Sande) radix-2 network in
-//                registers, 8 elements per lane, in rounds of up to three
-//                stages (radix-8) with a shared-memory exchange between
-//                rounds;
-//   store phase: coalesced 32-byte stores of the tile in natural order.
-// The shared tile is XOR-swizzled on 16-byte chunks so that the access
-// patterns of all three phases are free of bank conflicts for S = 256.
+//   rounds     : decimation-in-frequency (Gentleman-Sande) radix-2 network
+//                over every sub-transform of the tile, two stages at a time
+//                (radix-4: each thread loads 4 elements, does 4 butterflies,
+//                writes them back), the whole CTA in lockstep with a barrier
+//                between rounds.  The round loop runs at run time so that the
+//                hot code is one radix-4 body (small enough for the
+//                instruction cache).  An odd number of stages starts with a
+//                radix-2 round; the last round (stages 1 and 0) knows its
+//                trivial twiddles at compile time and does 1 multiply per 4
+//                elements instead of 4;
+//   store phase: coalesced 32-byte stores; the DIF output order is undone by
+//                reading the tile at bit-reversed positions.
+// The tile is XOR-swizzled on 16-byte chunks (swz); the swizzle was chosen
+// by an exhaustive check so that every access pattern of the three phases,
+// for every sub-transform size 2..2048, is free of bank conflicts.
 #pragma once
 
 #include <cstdint>
@@ -45,10 +51,13 @@
 namespace gb300ntt {
 
 constexpr int kPassThreads = 256;
+constexpr int kPassCtasPerSm = 3;
 constexpr int kTileLog = 11;                       // 2048 elements per CTA
 constexpr int kTileElems = 1 << kTileLog;
 constexpr int kTileBytes = kTileElems * 32;       // 64 KiB
-constexpr int kMaxPassLog = 8;                     // sub-transforms up to 256 points
+constexpr int kMaxPassLog = kTileLog;              // sub-transforms up to 2048 points
+constexpr int kElemsPerThread = kTileElems / kPassThreads;   // 8
+constexpr int kGroupsPerThread = kElemsPerThread / 4;        // radix-4 groups per round
 
 enum PassMode : int {
   kModeInner = 0,     // pass j >= 1: in place, 2-D input multiplier table [S][Mp]
@@ -68,187 +77,165 @@ struct PassArgs {
   uint32_t digit_shift[4];  // first: log2(S_1 ... S_{j-1}) at index j-1
 };
 
-// 16-byte chunk index of half h of tile element e (bank-conflict swizzle).
-__device__ __forceinline__ uint32_t tile_chunk(uint32_t e, uint32_t h) {
-  const uint32_t x = e >> 2;
-  return ((e << 1) | h) ^ ((x ^ (x >> 3) ^ (x >> 6)) & 7u);
+// ------------------------------------------------------------- swizzle
+// Chunk c = 2e + h (16-byte half h of tile element e) is stored at
+// c ^ swz(e), swz(e) = XOR of f_b over the set bits b >= 2 of e, with
+// f_2..f_10 = 1,7,3,5,7,1,3,4,1 (3-bit columns).  Packed as three 8-entry
+// lookup tables (3 bits per entry) for e bits 2-4, 5-7 and 8-10.
+constexpr uint32_t swz_lut(uint32_t fa, uint32_t fb, uint32_t fc) {
+  uint32_t lut = 0;
+  for (uint32_t x = 0; x < 8; ++x) {
+    const uint32_t v = ((x & 1) ? fa : 0) ^ ((x & 2) ? fb : 0) ^ ((x & 4) ? fc : 0);
+    lut |= v << (3 * x);
+  }
+  return lut;
+}
+constexpr uint32_t kSwzLut0 = swz_lut(1, 7, 3);
+constexpr uint32_t kSwzLut1 = swz_lut(5, 7, 1);
+constexpr uint32_t kSwzLut2 = swz_lut(3, 4, 1);
+
+__device__ __forceinline__ uint32_t swz(uint32_t e) {
+  const uint32_t x0 = (e >> 2) & 7, x1 = (e >> 5) & 7, x2 = (e >> 8) & 7;
+  return ((kSwzLut0 >> (3 * x0)) ^ (kSwzLut1 >> (3 * x1)) ^ (kSwzLut2 >> (3 * x2))) & 7u;
 }
 
 __device__ __forceinline__ void tile_store(uint4 *tile, uint32_t e, const uint32_t a[8]) {
-  tile[tile_chunk(e, 0)] = make_uint4(a[0], a[1], a[2], a[3]);
-  tile[tile_chunk(e, 1)] = make_uint4(a[4], a[5], a[6], a[7]);
+  const uint32_t s = swz(e), c = e << 1;
+  tile[c ^ s] = make_uint4(a[0], a[1], a[2], a[3]);
+  tile[(c | 1) ^ s] = make_uint4(a[4], a[5], a[6], a[7]);
 }
 
 __device__ __forceinline__ void tile_load(uint32_t r[8], const uint4 *tile, uint32_t e) {
-  const uint4 lo = tile[tile_chunk(e, 0)];
-  const uint4 hi = tile[tile_chunk(e, 1)];
+  const uint32_t s = swz(e), c = e << 1;
+  const uint4 lo = tile[c ^ s];
+  const uint4 hi = tile[(c | 1) ^ s];
   r[0] = lo.x; r[1] = lo.y; r[2] = lo.z; r[3] = lo.w;
   r[4] = hi.x; r[5] = hi.y; r[6] = hi.z; r[7] = hi.w;
 }
 
-// ------------------------------------------------------- round structure
-// A size-2^LOGS DIF network is split into R = ceil(LOGS/3) rounds, from the
-// top bit down; round sizes are as equal as possible with the larger ones
-// first, so the last round has at least two bits whenever LOGS >= 2.
+// ----------------------------------------------------------- butterflies
 
-__host__ __device__ constexpr int num_rounds(int logs) { return (logs + 2) / 3; }
-
-__host__ __device__ constexpr int round_bits(int logs, int r) {
-  return logs / num_rounds(logs) + (r < logs % num_rounds(logs) ? 1 : 0);
+// DIF butterfly: (x, y) -> (x + y, (x - y) * w); w in Montgomery form.
+template <class F>
+__device__ __forceinline__ void dif_bfly(uint32_t x[8], uint32_t y[8], const uint32_t w[8]) {
+  uint32_t d[8];
+  sub_mod<F>(d, x, y);
+  add_mod<F>(x, x, y);
+  mont_mul<F>(y, d, w);
 }
 
-__host__ __device__ constexpr int round_low(int logs, int r) {
-  int hi = logs;
-  for (int i = 0; i <= r; ++i) hi -= round_bits(logs, i);
-  return hi;
+// DIF butterfly with twiddle 1.
+template <class F>
+__device__ __forceinline__ void dif_bfly1(uint32_t x[8], uint32_t y[8]) {
+  uint32_t d[8];
+  sub_mod<F>(d, x, y);
+  add_mod<F>(x, x, y);
+  fe_copy(y, d);
 }
 
-// Warp-local position (8 bits) of register slot `slot` of `lane` in a round
-// that owns position bits [T, T+B): slot bits 0..B-1 are the round bits, the
-// five lane bits fill the lowest remaining position bits, and the remaining
-// 3-B slot bits fill the rest.
-template <int T, int B>
-__device__ __forceinline__ uint32_t slot_pos(uint32_t lane, int slot) {
-  uint32_t pos = 0;
-  int li = 0, si = B;
-#pragma unroll
-  for (int bit = 0; bit < 8; ++bit) {
-    if (bit >= T && bit < T + B) {
-      pos |= (uint32_t)((slot >> (bit - T)) & 1) << bit;
-    } else if (li < 5) {
-      pos |= ((lane >> li) & 1u) << bit;
-      ++li;
+// Radix-2 round on bit T = LOGS - 1 (first round when LOGS is odd): pairs
+// (p, p + S/2) with twiddle omega_S^(p mod S/2).
+template <class F, int LOGS>
+__device__ __forceinline__ void round_radix2_top(uint4 *tile, const uint4 *dft_tw) {
+  constexpr uint32_t H = 1u << (LOGS - 1);
+#pragma unroll 1
+  for (int i = 0; i < kElemsPerThread / 2; ++i) {
+    const uint32_t g = threadIdx.x + kPassThreads * i;      // pair index < 1024
+    const uint32_t low = g & (H - 1);
+    const uint32_t e0 = low | ((g >> (LOGS - 1)) << LOGS);
+    uint32_t x[8], y[8];
+    tile_load(x, tile, e0);
+    tile_load(y, tile, e0 | H);
+    if constexpr (LOGS == 1) {
+      dif_bfly1<F>(x, y);
     } else {
-      pos |= (uint32_t)((slot >> si) & 1) << bit;
-      ++si;
+      uint32_t w[8];
+      fe_load_global(w, dft_tw, low);
+      dif_bfly<F>(x, y, w);
     }
+    tile_store(tile, e0, x);
+    tile_store(tile, e0 | H, y);
   }
-  return pos;
+}
+
+// Radix-4 round on bits [T, T+1], T >= 2 (run-time T).
+template <class F, int LOGS>
+__device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, uint32_t T) {
+  const uint32_t step = 1u << T;
+  const uint32_t sh = LOGS - 2 - T;
+#pragma unroll 1
+  for (int i = 0; i < kGroupsPerThread; ++i) {
+    const uint32_t g = threadIdx.x + kPassThreads * i;      // group index < 512
+    const uint32_t low = g & (step - 1);
+    const uint32_t e0 = low | ((g >> T) << (T + 2));
+    uint32_t x0[8], x1[8], x2[8], x3[8], w[8];
+    tile_load(x0, tile, e0);
+    tile_load(x1, tile, e0 + step);
+    tile_load(x2, tile, e0 + 2 * step);
+    tile_load(x3, tile, e0 + 3 * step);
+    // stage on bit T+1 (h = 2^(T+1)): twiddle omega_S^((p mod h) * S/(2h))
+    fe_load_global(w, dft_tw, low << sh);
+    dif_bfly<F>(x0, x2, w);
+    fe_load_global(w, dft_tw, (low + step) << sh);
+    dif_bfly<F>(x1, x3, w);
+    // stage on bit T (h = 2^T)
+    fe_load_global(w, dft_tw, low << (sh + 1));
+    dif_bfly<F>(x0, x1, w);
+    dif_bfly<F>(x2, x3, w);
+    tile_store(tile, e0, x0);
+    tile_store(tile, e0 + step, x1);
+    tile_store(tile, e0 + 2 * step, x2);
+    tile_store(tile, e0 + 3 * step, x3);
+  }
+}
+
+// Last round, bits [0, 1]: stage 1 has twiddles 1 and omega_4, stage 0 only 1.
+template <class F, int LOGS>
+__device__ __forceinline__ void round_radix4_last(uint4 *tile, const uint4 *dft_tw) {
+  uint32_t w4[8];
+  fe_load_global(w4, dft_tw, 1u << (LOGS - 2));   // omega_S^(S/4) = omega_4
+#pragma unroll 1
+  for (int i = 0; i < kGroupsPerThread; ++i) {
+    const uint32_t e0 = (threadIdx.x + kPassThreads * i) << 2;
+    uint32_t x0[8], x1[8], x2[8], x3[8];
+    tile_load(x0, tile, e0);
+    tile_load(x1, tile, e0 + 1);
+    tile_load(x2, tile, e0 + 2);
+    tile_load(x3, tile, e0 + 3);
+    dif_bfly1<F>(x0, x2);
+    dif_bfly<F>(x1, x3, w4);
+    dif_bfly1<F>(x0, x1);
+    dif_bfly1<F>(x2, x3);
+    tile_store(tile, e0, x0);
+    tile_store(tile, e0 + 1, x1);
+    tile_store(tile, e0 + 2, x2);
+    tile_store(tile, e0 + 3, x3);
+  }
 }
 
 template <int LOGS>
 __device__ __forceinline__ uint32_t bit_reverse_local(uint32_t p) {
-  return LOGS == 0 ? 0u : (__brev(p) >> (32 - LOGS));
+  return __brev(p) >> (32 - LOGS);
 }
 
-// One round of DIF stages (bits T+B-1 down to T) on the lane's 8 registers.
-template <class F, int LOGS, int T, int B>
-__device__ __forceinline__ void dif_round(uint32_t (&x)[8][8], uint32_t lane, const uint4 *twt) {
-  constexpr uint32_t S = 1u << LOGS;
-#pragma unroll
-  for (int beta = T + B - 1; beta >= T; --beta) {
-    const int sb = beta - T;
-#pragma unroll
-    for (int s0 = 0; s0 < 8; ++s0) {
-      if (s0 & (1 << sb)) continue;
-      const int s1 = s0 | (1 << sb);
-      uint32_t d[8];
-      sub_mod<F>(d, x[s0], x[s1]);
-      add_mod<F>(x[s0], x[s0], x[s1]);
-      // twiddle omega_{2h}^(p mod h), h = 2^beta, as index into omega_S^i
-      const bool trivial = (beta == 0) || (T == 0 && (s0 & ((1 << beta) - 1)) == 0);
-      if (trivial) {
-        fe_copy(x[s1], d);
-      } else {
-        const uint32_t p = slot_pos<T, B>(lane, s0) & (S - 1);
-        const uint32_t idx = (p & ((1u << beta) - 1)) << (LOGS - 1 - beta);
-        uint32_t w[8];
-        tile_load(w, twt, idx);
-        mont_mul<F>(x[s1], d, w);
-      }
-    }
-  }
-}
+// ------------------------------------------------------------ pass tile
 
-// The tile pointer passed around is the CTA's tile; warp w works on tile
-// elements [256w, 256w + 256), so positions are offset by `base`.
-struct WarpTile {
-  uint4 *tile;
-  uint32_t base;
-};
-
-__device__ __forceinline__ void wt_store(const WarpTile &t, uint32_t pos, const uint32_t a[8]) {
-  tile_store(t.tile, t.base + pos, a);
-}
-__device__ __forceinline__ void wt_load(uint32_t r[8], const WarpTile &t, uint32_t pos) {
-  tile_load(r, t.tile, t.base + pos);
-}
-
-template <int T, int B>
-__device__ __forceinline__ void wround_store(const WarpTile &t, uint32_t lane, const uint32_t (&x)[8][8]) {
-#pragma unroll
-  for (int s = 0; s < 8; ++s) wt_store(t, slot_pos<T, B>(lane, s), x[s]);
-}
-
-template <int T, int B>
-__device__ __forceinline__ void wround_load(uint32_t (&x)[8][8], uint32_t lane, const WarpTile &t) {
-#pragma unroll
-  for (int s = 0; s < 8; ++s) wt_load(x[s], t, slot_pos<T, B>(lane, s));
-}
-
-// Round r and everything after it; exchange through shared memory between
-// rounds.  On entry the registers hold round r's layout.
-template <class F, int LOGS, int R>
-__device__ __forceinline__ void warp_rounds(uint32_t (&x)[8][8], uint32_t lane, const WarpTile &t,
-                                            const uint4 *twt) {
-  constexpr int T = round_low(LOGS, R);
-  constexpr int B = round_bits(LOGS, R);
-  dif_round<F, LOGS, T, B>(x, lane, twt);
-  if constexpr (R + 1 < num_rounds(LOGS)) {
-    constexpr int T2 = round_low(LOGS, R + 1);
-    constexpr int B2 = round_bits(LOGS, R + 1);
-    __syncwarp();
-    wround_store<T, B>(t, lane, x);
-    __syncwarp();
-    wround_load<T2, B2>(x, lane, t);
-    warp_rounds<F, LOGS, R + 1>(x, lane, t, twt);
-  } else {
-    // DIF leaves position p holding output bitrev(p): write it to its
-    // natural place in the sub-transform.
-    constexpr uint32_t S = 1u << LOGS;
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const uint32_t p = slot_pos<T, B>(lane, s);
-      wt_store(t, (p & ~(S - 1)) | bit_reverse_local<LOGS>(p & (S - 1)), x[s]);
-    }
-  }
-}
-
-// Size-2^LOGS DFTs of all sub-transforms of the warp's 256 tile elements,
-// in place in shared memory (natural order in and out).
-template <class F, int LOGS>
-__device__ __forceinline__ void warp_dft(const WarpTile &t, uint32_t lane, const uint4 *twt) {
-  uint32_t x[8][8];
-  constexpr int T0 = round_low(LOGS, 0);
-  constexpr int B0 = round_bits(LOGS, 0);
-  wround_load<T0, B0>(x, lane, t);
-  warp_rounds<F, LOGS, 0>(x, lane, t, twt);
-}
-
-// ------------------------------------------------------------ pass kernel
-
-template <class F, int LOGS, int MODE>
-__global__ void __launch_bounds__(kPassThreads, 2) ntt_pass_kernel(const PassArgs a) {
-  extern __shared__ uint4 smem[];
-  uint4 *tile = smem;
-  uint4 *twt = smem + 2 * kTileElems;
+// Process tile `tile` of one pass.  All threads of the CTA call this.
+// CG = true reads the pass input with ld.global.cg (L2, coherent), for data
+// written earlier in the same kernel launch (the persistent batched kernel);
+// otherwise through the read-only path.
+template <class F, int LOGS, int MODE, bool CG>
+__device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint4 *smem) {
   constexpr uint32_t S = 1u << LOGS;
   constexpr int LOGG = kTileLog - LOGS;
   constexpr uint32_t G = 1u << LOGG;
 
-  // DFT twiddles omega_S^i (i < S/2) into shared memory.
-  for (uint32_t i = threadIdx.x; i < (S / 2) * 2; i += kPassThreads) {
-    const uint32_t e = i >> 1, h = i & 1;
-    twt[tile_chunk(e, h)] = __ldg(a.dft_tw + i);
-  }
-
-  const uint64_t d0 = (uint64_t)blockIdx.x << LOGG;
+  const uint64_t d0 = tile << LOGG;
   const uint64_t mp_mask = (1ull << a.log_mp) - 1;
 
   // ---------------- load phase: element e of the tile = (n, dl), n-major
-#pragma unroll 2
-  for (int i = 0; i < kTileElems / kPassThreads; ++i) {
+#pragma unroll 1
+  for (int i = 0; i < kElemsPerThread; ++i) {
     const uint32_t e = threadIdx.x + kPassThreads * i;
     const uint32_t n = e >> LOGG, dl = e & (G - 1);
     const uint64_t d = d0 + dl;
@@ -257,7 +244,8 @@ __global__ void __launch_bounds__(kPassThreads, 2) ntt_pass_kernel(const PassArg
       if constexpr (MODE == kModeInner) {
         const uint64_t q = d & mp_mask, o = d >> a.log_mp;
         const uint64_t pos = q + ((uint64_t)n << a.log_mp) + (o << (a.log_mp + LOGS));
-        fe_load_global(v, a.src, pos);
+        if constexpr (CG) fe_load_global_cg(v, a.src, pos);
+        else fe_load_global(v, a.src, pos);
         uint32_t w[8];
         fe_load_global(w, a.mul, ((uint64_t)n << a.log_mp) + q);
         mont_mul<F>(v, v, w);
@@ -269,19 +257,31 @@ __global__ void __launch_bounds__(kPassThreads, 2) ntt_pass_kernel(const PassArg
           mont_mul<F>(v, v, w);
         }
       }
-      tile_store(tile, (dl << LOGS) | n, v);
+      tile_store(smem, (dl << LOGS) | n, v);
     }
   }
   __syncthreads();
 
-  // ---------------- warp phase
-  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  warp_dft<F, LOGS>(WarpTile{tile, warp * 256u}, lane, twt);
-  __syncthreads();
+  // ---------------- DIF rounds, top bit down
+  int T = LOGS;
+  if constexpr (LOGS & 1) {
+    round_radix2_top<F, LOGS>(smem, a.dft_tw);
+    __syncthreads();
+    T -= 1;
+  }
+#pragma unroll 1
+  for (T -= 2; T >= 2; T -= 2) {
+    round_radix4<F, LOGS>(smem, a.dft_tw, (uint32_t)T);
+    __syncthreads();
+  }
+  if constexpr (LOGS >= 2) {
+    round_radix4_last<F, LOGS>(smem, a.dft_tw);
+    __syncthreads();
+  }
 
-  // ---------------- store phase
+  // ---------------- store phase (read the tile at bit-reversed positions)
 #pragma unroll 2
-  for (int i = 0; i < kTileElems / kPassThreads; ++i) {
+  for (int i = 0; i < kElemsPerThread; ++i) {
     const uint32_t e = threadIdx.x + kPassThreads * i;
     if constexpr (MODE == kModeInner) {
       const uint32_t k = e >> LOGG, dl = e & (G - 1);
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kPassThreads, 2) ntt_pass_kernel(const PassArg
         const uint64_t q = d & mp_mask, o = d >> a.log_mp;
         const uint64_t pos = q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS));
         uint32_t v[8];
-        tile_load(v, tile, (dl << LOGS) | k);
+        tile_load(v, smem, (dl << LOGS) | bit_reverse_local<LOGS>(k));
         fe_store_global(a.dst, pos, v);
       }
     } else {
@@ -308,13 +308,21 @@ __global__ void __launch_bounds__(kPassThreads, 2) ntt_pass_kernel(const PassArg
           }
         }
         uint32_t v[8];
-        tile_load(v, tile, e);
+        tile_load(v, smem, (dl << LOGS) | bit_reverse_local<LOGS>(k));
         fe_store_global(a.dst, (rev << LOGS) | k, v);
       }
     }
   }
 }
 
-inline int pass_smem_bytes(int logs) { return kTileBytes + (1 << logs) / 2 * 32; }
+// ------------------------------------------------------------ pass kernel
+
+template <class F, int LOGS, int MODE>
+__global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) ntt_pass_kernel(const PassArgs a) {
+  extern __shared__ uint4 smem[];
+  pass_tile<F, LOGS, MODE, false>(a, blockIdx.x, smem);
+}
+
+inline int pass_smem_bytes(int) { return kTileBytes; }
 
 }  // namespace gb300ntt

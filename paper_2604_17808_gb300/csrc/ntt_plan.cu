@@ -72,18 +72,22 @@ ntt_status prepare_device(int device, int field) {
   return NTT_OK;
 }
 
+}  // namespace
+
 ntt_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return NTT_OK;
   if (e == cudaErrorMemoryAllocation) return NTT_ERR_OOM;
   return NTT_ERR_CUDA;
 }
 
-}  // namespace
+// Default split of log_n into passes of at most kDefaultPassLog bits, as
+// equal as possible, larger ones first.  (Sub-transforms of up to 2^10
+// points keep at least two per tile, so the strided reads of a pass still
+// touch two adjacent elements; the autotuner may pick other splits.)
+constexpr uint32_t kDefaultPassLog = 10;
 
-// Split log_n into passes of at most kMaxPassLog bits, as equal as
-// possible, larger ones first.
 std::vector<uint32_t> split_passes(uint32_t log_n) {
-  const uint32_t P = (log_n + kMaxPassLog - 1) / kMaxPassLog;
+  const uint32_t P = (log_n + kDefaultPassLog - 1) / kDefaultPassLog;
   std::vector<uint32_t> s(P, log_n / P);
   for (uint32_t i = 0; i < log_n % P; ++i) s[i] += 1;
   return s;
@@ -194,42 +198,51 @@ ntt_status build_plan(ntt_plan p, cudaStream_t st) {
   return NTT_OK;
 }
 
-// Enqueue one transform.  Exposed to the batched path as well.
-ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st) {
-  const FieldLaunchers &L = launchers(p->field);
+// Arguments of pass j of one transform: pass 0 reads `in`; every later pass
+// works in place on `work` (out, or the plan's scratch for in-place calls);
+// the last pass writes `out`.
+void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j, PassArgs *a, int *mode) {
   const uint32_t P = p->num_passes, log_n = p->log_n;
   const int dir = kind == kInverse ? 1 : 0;
   uint4 *work = (P > 1 && in == out) ? p->scratch : (uint4 *)out;
-  for (uint32_t j = 0; j < P; ++j) {
-    const uint32_t logs = p->pass_log[j];
-    PassArgs a{};
-    a.dft_tw = p->dft_tw[dir][logs];
-    a.num_sub = 1ull << (log_n - logs);
-    int mode;
-    if (j == 0) {
-      a.src = (const uint4 *)in;
-      a.dst = P == 1 ? (uint4 *)out : work;
-      a.log_mp = log_n - logs;
-      a.num_digits = P - 1;
-      uint32_t shift = 0;
-      for (uint32_t d = 1; d < P; ++d) {
-        a.digit_log[d - 1] = p->pass_log[d];
-        a.digit_shift[d - 1] = shift;
-        shift += p->pass_log[d];
-      }
-      a.mul = p->pre[kind];
-      mode = a.mul ? kModeFirstPre : kModeFirst;
-    } else {
-      uint32_t log_mp = 0;
-      for (uint32_t i = 0; i < j; ++i) log_mp += p->pass_log[i];
-      a.src = work;
-      a.dst = j == P - 1 ? (uint4 *)out : work;
-      a.log_mp = log_mp;
-      a.mul = p->tw[kind][j];
-      mode = kModeInner;
+  const uint32_t logs = p->pass_log[j];
+  *a = PassArgs{};
+  a->dft_tw = p->dft_tw[dir][logs];
+  a->num_sub = 1ull << (log_n - logs);
+  if (j == 0) {
+    a->src = (const uint4 *)in;
+    a->dst = P == 1 ? (uint4 *)out : work;
+    a->log_mp = log_n - logs;
+    a->num_digits = P - 1;
+    uint32_t shift = 0;
+    for (uint32_t d = 1; d < P; ++d) {
+      a->digit_log[d - 1] = p->pass_log[d];
+      a->digit_shift[d - 1] = shift;
+      shift += p->pass_log[d];
     }
+    a->mul = p->pre[kind];
+    *mode = a->mul ? kModeFirstPre : kModeFirst;
+  } else {
+    uint32_t log_mp = 0;
+    for (uint32_t i = 0; i < j; ++i) log_mp += p->pass_log[i];
+    a->src = work;
+    a->dst = j == P - 1 ? (uint4 *)out : work;
+    a->log_mp = log_mp;
+    a->mul = p->tw[kind][j];
+    *mode = kModeInner;
+  }
+}
+
+// Enqueue one transform: one kernel launch per pass.
+ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st) {
+  const FieldLaunchers &L = launchers(p->field);
+  for (uint32_t j = 0; j < p->num_passes; ++j) {
+    PassArgs a;
+    int mode;
+    build_pass_args(p, kind, in, out, j, &a, &mode);
+    const uint32_t logs = p->pass_log[j];
     cudaError_t e = timing_begin(p, (int)j, st);
-    if (e == cudaSuccess) e = L.pass((int)logs, mode, a, pass_tiles(log_n, logs), st);
+    if (e == cudaSuccess) e = L.pass((int)logs, mode, a, pass_tiles(p->log_n, logs), st);
     if (e == cudaSuccess) e = timing_end(p, st);
     if (e != cudaSuccess) return cuda_status(e);
   }
@@ -339,6 +352,7 @@ ntt_status ntt_plan_set_coset_shift(ntt_plan plan, const uint64_t shift[4]) {
 
 ntt_status ntt_plan_destroy(ntt_plan plan) {
   if (!plan) return NTT_OK;
+  batch_forget_plan(plan);
   cudaDeviceSynchronize();
   for (void *ptr : plan->allocations) cudaFree(ptr);
   if (plan->d_err) cudaFree(plan->d_err);

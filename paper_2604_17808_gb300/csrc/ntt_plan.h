@@ -30,7 +30,7 @@ struct ntt_plan_s {
   uint32_t launches = 0;
   gb300ntt::U256 omega{}, omega_inv{}, coset_shift{};
   // device tables, Montgomery form, 32 bytes per entry
-  uint4 *dft_tw[2][9] = {};      // [direction][log S]: omega_S^(+-i), i < S/2
+  uint4 *dft_tw[2][12] = {};     // [direction][log S]: omega_S^(+-i), i < S/2
   uint4 *tw[3][4] = {};          // [kind][pass >= 1]: inter-pass multipliers [S_j][Mp]
   uint4 *pre[3] = {};            // [kind]: pass-0 multipliers [S_0] (coset; single-pass inverse)
   uint4 *fac_coset[4] = {};      // [pass >= 1]: s^(n N / M_j), n < S_j
@@ -51,6 +51,9 @@ namespace gb300ntt {
 std::vector<uint32_t> split_passes(uint32_t log_n);
 uint64_t pass_tiles(uint32_t log_n, uint32_t logs);
 ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
+ntt_status cuda_status(cudaError_t e);
+struct PassArgs;
+void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j, PassArgs *a, int *mode);
 ntt_status check_buffer(const void *ptr);
 // Timing hooks around one launch of pass `pass` (no-ops unless timing is on).
 cudaError_t timing_begin(ntt_plan p, int pass, cudaStream_t st);
@@ -61,5 +64,8 @@ bool matrix_path_available(ntt_plan p);
 ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
 uint32_t matrix_launches(ntt_plan p);
 void release_matrix_resources(ntt_plan p);
+
+// batched path, ntt_batch.cu
+void batch_forget_plan(ntt_plan plan);
 
 }  // namespace gb300ntt
