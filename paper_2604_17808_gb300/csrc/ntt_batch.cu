@@ -113,7 +113,7 @@ ntt_status build_part(const std::vector<JobKey> &jobs, int field, Part *part) {
       s.logs = j.plan->pass_log[level];
       s.mode = (uint32_t)mode;
       s.first_item = item;
-      s.num_tiles = (uint32_t)pass_tiles(j.plan->log_n, s.logs);
+      s.num_tiles = (uint32_t)pass_tiles(j.plan->log_n, s.logs, kTileLog);
       if (level > 0) {
         s.dep_seg = seg_of[i][level - 1];
         s.dep_tiles = segs[s.dep_seg].num_tiles;

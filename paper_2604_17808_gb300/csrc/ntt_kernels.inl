@@ -80,9 +80,9 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
 template <int LOGS>
 __device__ __forceinline__ void batch_tile_logs(const BatchSeg &sg, uint64_t tile, uint4 *smem) {
   switch (sg.mode) {
-    case kModeInner: pass_tile<F, LOGS, kModeInner, true>(sg.a, tile, smem); break;
-    case kModeFirst: pass_tile<F, LOGS, kModeFirst, true>(sg.a, tile, smem); break;
-    default: pass_tile<F, LOGS, kModeFirstPre, true>(sg.a, tile, smem); break;
+    case kModeInner: pass_tile<F, LOGS, kModeInner, true, 11>(sg.a, tile, smem); break;
+    case kModeFirst: pass_tile<F, LOGS, kModeFirst, true, 11>(sg.a, tile, smem); break;
+    default: pass_tile<F, LOGS, kModeFirstPre, true, 11>(sg.a, tile, smem); break;
   }
 }
 
@@ -163,66 +163,84 @@ cudaError_t batch(const BatchLaunch &b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int LOGS, int MODE>
+template <int LOGS, int MODE, int TL>
 cudaError_t set_pass_attr() {
-  return cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              pass_smem_bytes(LOGS));
+  return cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TileCfg<TL>::kBytes);
 }
 
-template <int LOGS>
+template <int LOGS, int TL>
 cudaError_t set_pass_attrs() {
-  cudaError_t e = set_pass_attr<LOGS, kModeInner>();
-  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirst>();
-  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirstPre>();
+  cudaError_t e = set_pass_attr<LOGS, kModeInner, TL>();
+  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirst, TL>();
+  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirstPre, TL>();
+  return e;
+}
+
+template <int TL>
+cudaError_t set_all_pass_attrs() {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = set_pass_attrs<1, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<2, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<3, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<4, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<5, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<6, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<7, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<8, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<9, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<10, TL>();
+  if constexpr (TL >= 11) {
+    if (e == cudaSuccess) e = set_pass_attrs<11, TL>();
+  }
   return e;
 }
 
 cudaError_t prepare() {
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = set_pass_attrs<1>();
-  if (e == cudaSuccess) e = set_pass_attrs<2>();
-  if (e == cudaSuccess) e = set_pass_attrs<3>();
-  if (e == cudaSuccess) e = set_pass_attrs<4>();
-  if (e == cudaSuccess) e = set_pass_attrs<5>();
-  if (e == cudaSuccess) e = set_pass_attrs<6>();
-  if (e == cudaSuccess) e = set_pass_attrs<7>();
-  if (e == cudaSuccess) e = set_pass_attrs<8>();
-  if (e == cudaSuccess) e = set_pass_attrs<9>();
-  if (e == cudaSuccess) e = set_pass_attrs<10>();
-  if (e == cudaSuccess) e = set_pass_attrs<11>();
+  cudaError_t e = set_all_pass_attrs<11>();
+  if (e == cudaSuccess) e = set_all_pass_attrs<10>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
   return e;
 }
 
-template <int LOGS>
+template <int LOGS, int TL>
 cudaError_t pass_logs(int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
-  const dim3 grid((unsigned)tiles), block(kPassThreads);
-  const int smem = pass_smem_bytes(LOGS);
+  const dim3 grid((unsigned)tiles), block(TileCfg<TL>::kThreads);
+  const int smem = TileCfg<TL>::kBytes;
   switch (mode) {
-    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner><<<grid, block, smem, st>>>(a); break;
-    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst><<<grid, block, smem, st>>>(a); break;
-    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre><<<grid, block, smem, st>>>(a); break;
+    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner, TL><<<grid, block, smem, st>>>(a); break;
+    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst, TL><<<grid, block, smem, st>>>(a); break;
+    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre, TL><<<grid, block, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t pass(int logs, int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+template <int TL>
+cudaError_t pass_tl(int logs, int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
   switch (logs) {
-    case 1: return pass_logs<1>(mode, a, tiles, st);
-    case 2: return pass_logs<2>(mode, a, tiles, st);
-    case 3: return pass_logs<3>(mode, a, tiles, st);
-    case 4: return pass_logs<4>(mode, a, tiles, st);
-    case 5: return pass_logs<5>(mode, a, tiles, st);
-    case 6: return pass_logs<6>(mode, a, tiles, st);
-    case 7: return pass_logs<7>(mode, a, tiles, st);
-    case 8: return pass_logs<8>(mode, a, tiles, st);
-    case 9: return pass_logs<9>(mode, a, tiles, st);
-    case 10: return pass_logs<10>(mode, a, tiles, st);
-    case 11: return pass_logs<11>(mode, a, tiles, st);
+    case 1: return pass_logs<1, TL>(mode, a, tiles, st);
+    case 2: return pass_logs<2, TL>(mode, a, tiles, st);
+    case 3: return pass_logs<3, TL>(mode, a, tiles, st);
+    case 4: return pass_logs<4, TL>(mode, a, tiles, st);
+    case 5: return pass_logs<5, TL>(mode, a, tiles, st);
+    case 6: return pass_logs<6, TL>(mode, a, tiles, st);
+    case 7: return pass_logs<7, TL>(mode, a, tiles, st);
+    case 8: return pass_logs<8, TL>(mode, a, tiles, st);
+    case 9: return pass_logs<9, TL>(mode, a, tiles, st);
+    case 10: return pass_logs<10, TL>(mode, a, tiles, st);
+    case 11:
+      if constexpr (TL >= 11) return pass_logs<11, TL>(mode, a, tiles, st);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t pass(int logs, int mode, int tl, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  if (tl == 11) return pass_tl<11>(logs, mode, a, tiles, st);
+  if (tl == 10) return pass_tl<10>(logs, mode, a, tiles, st);
+  return cudaErrorInvalidValue;
 }
 
 unsigned grid_for(uint64_t count) {

@@ -20,9 +20,10 @@
 // After the last pass the buffer holds X in natural order.  Coset and
 // inverse scale factors are folded into the same per-element multipliers.
 //
-// Work split on the GPU: one CTA (256 threads) owns a tile of 2048 elements
-// (64 KiB of shared memory) = G = 2048/S sub-transforms with consecutive
-// sub-transform index.
+// Work split on the GPU: one CTA owns a tile of 2^TL elements in shared
+// memory (TL = 11: 2048 elements, 256 threads; TL = 10: 1024 elements, 128
+// threads) = G = 2^TL / S sub-transforms with consecutive sub-transform
+// index.
 //   load phase : consecutive threads read consecutive 32-byte elements
 //                (coalesced), multiply by the input multiplier (pass >= 1:
 //                omega_M^(n q), read with the same coalesced pattern), and
@@ -50,14 +51,29 @@
 
 namespace gb300ntt {
 
-constexpr int kPassThreads = 256;
+// Two tile shapes, chosen per pass by the plan (and its autotuner):
+//   TL = 11: 2048 elements (64 KiB), 256 threads, 3 CTAs per SM;
+//   TL = 10: 1024 elements (32 KiB), 128 threads, 7 CTAs per SM (224 KiB of
+//            shared memory: 7168 elements resident per SM, so a 2^20-point
+//            pass fits in one wave of 152 SMs).
+// Every thread owns 8 elements in the load and store phases and two radix-4
+// groups per round.
+template <int TL>
+struct TileCfg {
+  static constexpr int kLog = TL;
+  static constexpr int kElems = 1 << TL;
+  static constexpr int kBytes = kElems * 32;
+  static constexpr int kThreads = kElems / 8;
+  static constexpr int kMinBlocks = TL == 11 ? 3 : 7;
+};
+
+constexpr int kPassThreads = 256;                  // batched kernel (TL = 11)
 constexpr int kPassCtasPerSm = 3;
-constexpr int kTileLog = 11;                       // 2048 elements per CTA
-constexpr int kTileElems = 1 << kTileLog;
-constexpr int kTileBytes = kTileElems * 32;       // 64 KiB
-constexpr int kMaxPassLog = kTileLog;              // sub-transforms up to 2048 points
-constexpr int kElemsPerThread = kTileElems / kPassThreads;   // 8
-constexpr int kGroupsPerThread = kElemsPerThread / 4;        // radix-4 groups per round
+constexpr int kTileLog = 11;
+constexpr int kTileBytes = TileCfg<11>::kBytes;
+constexpr int kMaxPassLog = 11;                    // sub-transforms up to 2048 points
+constexpr int kElemsPerThread = 8;
+constexpr int kGroupsPerThread = 2;                // radix-4 groups per thread per round
 
 enum PassMode : int {
   kModeInner = 0,     // pass j >= 1: in place, 2-D input multiplier table [S][Mp]
@@ -135,12 +151,12 @@ __device__ __forceinline__ void dif_bfly1(uint32_t x[8], uint32_t y[8]) {
 
 // Radix-2 round on bit T = LOGS - 1 (first round when LOGS is odd): pairs
 // (p, p + S/2) with twiddle omega_S^(p mod S/2).
-template <class F, int LOGS>
+template <class F, int LOGS, int TL>
 __device__ __forceinline__ void round_radix2_top(uint4 *tile, const uint4 *dft_tw) {
   constexpr uint32_t H = 1u << (LOGS - 1);
 #pragma unroll 1
   for (int i = 0; i < kElemsPerThread / 2; ++i) {
-    const uint32_t g = threadIdx.x + kPassThreads * i;      // pair index < 1024
+    const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;   // pair index
     const uint32_t low = g & (H - 1);
     const uint32_t e0 = low | ((g >> (LOGS - 1)) << LOGS);
     uint32_t x[8], y[8];
@@ -159,13 +175,13 @@ __device__ __forceinline__ void round_radix2_top(uint4 *tile, const uint4 *dft_t
 }
 
 // Radix-4 round on bits [T, T+1], T >= 2 (run-time T).
-template <class F, int LOGS>
+template <class F, int LOGS, int TL>
 __device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, uint32_t T) {
   const uint32_t step = 1u << T;
   const uint32_t sh = LOGS - 2 - T;
 #pragma unroll 1
   for (int i = 0; i < kGroupsPerThread; ++i) {
-    const uint32_t g = threadIdx.x + kPassThreads * i;      // group index < 512
+    const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;   // group index
     const uint32_t low = g & (step - 1);
     const uint32_t e0 = low | ((g >> T) << (T + 2));
     uint32_t x0[8], x1[8], x2[8], x3[8], w[8];
@@ -190,13 +206,13 @@ __device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, u
 }
 
 // Last round, bits [0, 1]: stage 1 has twiddles 1 and omega_4, stage 0 only 1.
-template <class F, int LOGS>
+template <class F, int LOGS, int TL>
 __device__ __forceinline__ void round_radix4_last(uint4 *tile, const uint4 *dft_tw) {
   uint32_t w4[8];
   fe_load_global(w4, dft_tw, 1u << (LOGS - 2));   // omega_S^(S/4) = omega_4
 #pragma unroll 1
   for (int i = 0; i < kGroupsPerThread; ++i) {
-    const uint32_t e0 = (threadIdx.x + kPassThreads * i) << 2;
+    const uint32_t e0 = (threadIdx.x + TileCfg<TL>::kThreads * i) << 2;
     uint32_t x0[8], x1[8], x2[8], x3[8];
     tile_load(x0, tile, e0);
     tile_load(x1, tile, e0 + 1);
@@ -224,11 +240,13 @@ __device__ __forceinline__ uint32_t bit_reverse_local(uint32_t p) {
 // CG = true reads the pass input with ld.global.cg (L2, coherent), for data
 // written earlier in the same kernel launch (the persistent batched kernel);
 // otherwise through the read-only path.
-template <class F, int LOGS, int MODE, bool CG>
+template <class F, int LOGS, int MODE, bool CG, int TL>
 __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint4 *smem) {
+  static_assert(LOGS <= TL, "sub-transform larger than the tile");
   constexpr uint32_t S = 1u << LOGS;
-  constexpr int LOGG = kTileLog - LOGS;
+  constexpr int LOGG = TL - LOGS;
   constexpr uint32_t G = 1u << LOGG;
+  constexpr int kThreads = TileCfg<TL>::kThreads;
 
   const uint64_t d0 = tile << LOGG;
   const uint64_t mp_mask = (1ull << a.log_mp) - 1;
@@ -236,7 +254,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
   // ---------------- load phase: element e of the tile = (n, dl), n-major
 #pragma unroll 1
   for (int i = 0; i < kElemsPerThread; ++i) {
-    const uint32_t e = threadIdx.x + kPassThreads * i;
+    const uint32_t e = threadIdx.x + kThreads * i;
     const uint32_t n = e >> LOGG, dl = e & (G - 1);
     const uint64_t d = d0 + dl;
     if (d < a.num_sub) {
@@ -265,24 +283,24 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
   // ---------------- DIF rounds, top bit down
   int T = LOGS;
   if constexpr (LOGS & 1) {
-    round_radix2_top<F, LOGS>(smem, a.dft_tw);
+    round_radix2_top<F, LOGS, TL>(smem, a.dft_tw);
     __syncthreads();
     T -= 1;
   }
 #pragma unroll 1
   for (T -= 2; T >= 2; T -= 2) {
-    round_radix4<F, LOGS>(smem, a.dft_tw, (uint32_t)T);
+    round_radix4<F, LOGS, TL>(smem, a.dft_tw, (uint32_t)T);
     __syncthreads();
   }
   if constexpr (LOGS >= 2) {
-    round_radix4_last<F, LOGS>(smem, a.dft_tw);
+    round_radix4_last<F, LOGS, TL>(smem, a.dft_tw);
     __syncthreads();
   }
 
   // ---------------- store phase (read the tile at bit-reversed positions)
 #pragma unroll 2
   for (int i = 0; i < kElemsPerThread; ++i) {
-    const uint32_t e = threadIdx.x + kPassThreads * i;
+    const uint32_t e = threadIdx.x + kThreads * i;
     if constexpr (MODE == kModeInner) {
       const uint32_t k = e >> LOGG, dl = e & (G - 1);
       const uint64_t d = d0 + dl;
@@ -317,12 +335,11 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
 
 // ------------------------------------------------------------ pass kernel
 
-template <class F, int LOGS, int MODE>
-__global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) ntt_pass_kernel(const PassArgs a) {
+template <class F, int LOGS, int MODE, int TL>
+__global__ void __launch_bounds__(TileCfg<TL>::kThreads, TileCfg<TL>::kMinBlocks)
+    ntt_pass_kernel(const PassArgs a) {
   extern __shared__ uint4 smem[];
-  pass_tile<F, LOGS, MODE, false>(a, blockIdx.x, smem);
+  pass_tile<F, LOGS, MODE, false, TL>(a, blockIdx.x, smem);
 }
-
-inline int pass_smem_bytes(int) { return kTileBytes; }
 
 }  // namespace gb300ntt

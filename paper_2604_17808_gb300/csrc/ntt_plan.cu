@@ -93,11 +93,15 @@ std::vector<uint32_t> split_passes(uint32_t log_n) {
   return s;
 }
 
-uint64_t pass_tiles(uint32_t log_n, uint32_t logs) {
+uint64_t pass_tiles(uint32_t log_n, uint32_t logs, uint32_t tl) {
   const uint64_t num_sub = 1ull << (log_n - logs);
-  const uint64_t g = 1ull << (kTileLog - logs);
+  const uint64_t g = 1ull << (tl - logs);
   return (num_sub + g - 1) / g;
 }
+
+// Default tile shape of a pass: the 1024-element tile (7 CTAs per SM) when
+// the sub-transform fits in it, else the 2048-element tile.
+uint32_t default_tile_log(uint32_t logs) { return logs <= 10 ? 10 : 11; }
 
 static ntt_status alloc_tab(ntt_plan p, uint4 **out, uint64_t elems) {
   void *ptr = nullptr;
@@ -154,7 +158,10 @@ ntt_status build_plan(ntt_plan p, cudaStream_t st) {
   const uint32_t log_n = p->log_n;
   const std::vector<uint32_t> passes = split_passes(log_n);
   p->num_passes = (uint32_t)passes.size();
-  for (uint32_t j = 0; j < p->num_passes; ++j) p->pass_log[j] = passes[j];
+  for (uint32_t j = 0; j < p->num_passes; ++j) {
+    p->pass_log[j] = passes[j];
+    p->pass_tl[j] = default_tile_log(passes[j]);
+  }
   const uint32_t P = p->num_passes;
 
   p->omega = F.root_of_unity(log_n);
@@ -242,7 +249,8 @@ ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cu
     build_pass_args(p, kind, in, out, j, &a, &mode);
     const uint32_t logs = p->pass_log[j];
     cudaError_t e = timing_begin(p, (int)j, st);
-    if (e == cudaSuccess) e = L.pass((int)logs, mode, a, pass_tiles(p->log_n, logs), st);
+    const uint32_t tl = p->pass_tl[j];
+    if (e == cudaSuccess) e = L.pass((int)logs, mode, (int)tl, a, pass_tiles(p->log_n, logs, tl), st);
     if (e == cudaSuccess) e = timing_end(p, st);
     if (e != cudaSuccess) return cuda_status(e);
   }

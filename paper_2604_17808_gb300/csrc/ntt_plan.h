@@ -27,6 +27,7 @@ struct ntt_plan_s {
   int sm_count = 0;
   uint32_t num_passes = 0;
   uint32_t pass_log[4] = {0, 0, 0, 0};
+  uint32_t pass_tl[4] = {11, 11, 11, 11};  // log2 tile size of each pass (10 or 11)
   uint32_t launches = 0;
   gb300ntt::U256 omega{}, omega_inv{}, coset_shift{};
   // device tables, Montgomery form, 32 bytes per entry
@@ -49,7 +50,7 @@ struct ntt_plan_s {
 namespace gb300ntt {
 
 std::vector<uint32_t> split_passes(uint32_t log_n);
-uint64_t pass_tiles(uint32_t log_n, uint32_t logs);
+uint64_t pass_tiles(uint32_t log_n, uint32_t logs, uint32_t tl);
 ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
 ntt_status cuda_status(cudaError_t e);
 struct PassArgs;
