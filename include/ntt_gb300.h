@@ -228,6 +228,64 @@ ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[4], uint64_t l
 ntt_status ntt_plan_poll_error(ntt_plan plan, uint32_t *code);
 
 /*
+ * Serving runtime (continuous batching).  A server keeps plans with their
+ * twiddle tables resident for both fields and every size in
+ * [min_log_n, max_log_n] (coset tables included), admits requests against
+ * a device-memory budget (resident tables + two N-element device buffers
+ * per admitted request), and runs admitted requests as batches (see
+ * ntt_batch_submit) on up to max_inflight streams, so that requests that
+ * arrive while others are on the GPU are admitted as soon as memory and a
+ * stream slot free up, and their work overlaps on the device.  A worker
+ * thread owned by the server does admission, dispatch and retirement.
+ *
+ * Requests use HOST buffers (page-locked for asynchronous copies): h_in is
+ * read and h_out written by the server between submit and completion; the
+ * caller must keep both alive until ntt_server_wait / ntt_server_query
+ * report completion.  Results are bit-identical to a transform run alone.
+ * Timestamps (seconds since server creation): arrive = submit, admit =
+ * device buffers reserved, finish = the batch's device-to-host copy done
+ * and observed by the worker; latency = finish - arrive.
+ */
+typedef struct ntt_server_s *ntt_server;
+
+typedef struct ntt_server_config {
+    uint64_t memory_budget_bytes; /* default 64 GiB (0 = default) */
+    uint32_t min_log_n;           /* default 12 */
+    uint32_t max_log_n;           /* default 24 */
+    uint32_t max_inflight;        /* batches in flight (streams), default 3, at most 16 */
+    uint32_t max_batch_jobs;      /* requests per batch, default 64 */
+    uint64_t max_batch_elements;  /* elements per batch, default 2^26 (a single larger request still runs) */
+} ntt_server_config;
+
+typedef struct ntt_server_stats {
+    uint64_t submitted;
+    uint64_t completed;
+    uint64_t batches;
+    uint64_t queued;              /* waiting for admission or dispatch */
+    uint64_t resident_bytes;      /* plans and twiddle tables */
+    uint64_t peak_device_bytes;   /* resident + request buffers, high-water mark */
+    uint64_t budget_bytes;
+} ntt_server_stats;
+
+/* cfg may be NULL (all defaults).  NTT_ERR_BUDGET if the resident tables
+ * plus one largest request exceed the budget. */
+ntt_status ntt_server_create(const ntt_server_config *cfg, ntt_server *out);
+/* Enqueue one request; *ticket identifies it.  Non-blocking. */
+ntt_status ntt_server_submit(ntt_server server, ntt_field field, ntt_kind kind, uint32_t log_n, const void *h_in,
+                             void *h_out, uint64_t *ticket);
+/* *done = 1 once h_out holds the result. */
+ntt_status ntt_server_query(ntt_server server, uint64_t ticket, int *done);
+/* Block until the request is done (NTT_ERR_TIMEOUT after timeout_s > 0). */
+ntt_status ntt_server_wait(ntt_server server, uint64_t ticket, double timeout_s);
+ntt_status ntt_server_request_times(ntt_server server, uint64_t ticket, double *arrive_s, double *admit_s,
+                                    double *finish_s);
+/* Forget a completed request (its record and timestamps). */
+ntt_status ntt_server_release(ntt_server server, uint64_t ticket);
+ntt_status ntt_server_get_stats(ntt_server server, ntt_server_stats *out);
+/* Finish every submitted request, then free the server. */
+ntt_status ntt_server_destroy(ntt_server server);
+
+/*
  * Diagnostic: element-wise Montgomery product of device vectors,
  * out[i] = a[i] * b[i] * 2^-256 mod M, the field multiplication every
  * butterfly uses (the paper's "radix Mont" baseline, Sec. 2.3.2: 8 32-bit

@@ -41,6 +41,18 @@ class PlanDesc(ctypes.Structure):
     ]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("min_log_n", ctypes.c_uint32),
+                ("max_log_n", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("max_batch_jobs", ctypes.c_uint32), ("max_batch_elements", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64),
+                ("peak_device_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("kind", ctypes.c_int32), ("in_", ctypes.c_void_p),
                 ("out", ctypes.c_void_p)]
@@ -72,6 +84,15 @@ _SIGS = {
     "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
     "ntt_plan_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ntt_plan_read_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U64)]),
+    "ntt_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)]),
+    "ntt_server_submit": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _U32, _VP, _VP, ctypes.POINTER(_U64)]),
+    "ntt_server_query": (ctypes.c_int, [_VP, _U64, ctypes.POINTER(ctypes.c_int)]),
+    "ntt_server_wait": (ctypes.c_int, [_VP, _U64, ctypes.c_double]),
+    "ntt_server_request_times": (ctypes.c_int, [_VP, _U64, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "ntt_server_release": (ctypes.c_int, [_VP, _U64]),
+    "ntt_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ServerStats)]),
+    "ntt_server_destroy": (ctypes.c_int, [_VP]),
     "ntt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ntt_version": (_U32, []),
 }
@@ -244,6 +265,52 @@ def ntt_plan_read_timing(plan: int) -> tuple[list[float], list[int]]:
     cnt = (_U64 * 4)()
     _check(load().ntt_plan_read_timing(plan, ms, cnt), "ntt_plan_read_timing")
     return list(ms), list(cnt)
+
+
+def ntt_server_create(memory_budget_bytes: int = 0, min_log_n: int = 0, max_log_n: int = 0,
+                      max_inflight: int = 0, max_batch_jobs: int = 0, max_batch_elements: int = 0) -> int:
+    cfg = ServerConfig(memory_budget_bytes, min_log_n, max_log_n, max_inflight, max_batch_jobs, max_batch_elements)
+    h = _VP()
+    _check(load().ntt_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ntt_server_create")
+    return int(h.value)
+
+
+def ntt_server_submit(server: int, field, kind, log_n: int, h_in, h_out) -> int:
+    t = _U64()
+    _check(load().ntt_server_submit(server, _field(field), _kind(kind), int(log_n), _ptr(h_in), _ptr(h_out),
+                                    ctypes.byref(t)), "ntt_server_submit")
+    return int(t.value)
+
+
+def ntt_server_query(server: int, ticket: int) -> bool:
+    d = ctypes.c_int()
+    _check(load().ntt_server_query(server, ticket, ctypes.byref(d)), "ntt_server_query")
+    return bool(d.value)
+
+
+def ntt_server_wait(server: int, ticket: int, timeout_s: float = 0.0) -> None:
+    _check(load().ntt_server_wait(server, ticket, float(timeout_s)), "ntt_server_wait")
+
+
+def ntt_server_request_times(server: int, ticket: int) -> tuple[float, float, float]:
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().ntt_server_request_times(server, ticket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "ntt_server_request_times")
+    return a.value, b.value, c.value
+
+
+def ntt_server_release(server: int, ticket: int) -> None:
+    _check(load().ntt_server_release(server, ticket), "ntt_server_release")
+
+
+def ntt_server_get_stats(server: int) -> dict:
+    st = ServerStats()
+    _check(load().ntt_server_get_stats(server, ctypes.byref(st)), "ntt_server_get_stats")
+    return {k: int(getattr(st, k)) for k, _ in ServerStats._fields_}
+
+
+def ntt_server_destroy(server: int) -> None:
+    _check(load().ntt_server_destroy(server), "ntt_server_destroy")
 
 
 def ntt_status_string(status: int) -> str:

@@ -88,14 +88,18 @@ ntt_status device_err_word(int dev, uint32_t **out) {
   return NTT_OK;
 }
 
-// Build the segment table of the jobs of one field and upload it.
-ntt_status build_part(const std::vector<JobKey> &jobs, int field, Part *part) {
+}  // namespace
+
+namespace gb300ntt {
+
+// Segment table of the jobs of one field: every pass of every job, ordered
+// by pass level (larger jobs first within a level).  Pure host code.
+std::vector<BatchSeg> build_segments(const std::vector<BatchJobRef> &jobs, int field, uint32_t *total_items) {
   std::vector<BatchSeg> segs;
   std::vector<std::vector<int>> seg_of(jobs.size());  // [job][pass] -> segment index
   uint32_t max_passes = 0;
-  for (const JobKey &j : jobs)
+  for (const BatchJobRef &j : jobs)
     if (j.plan->field == field) max_passes = std::max(max_passes, j.plan->num_passes);
-  // within a level, larger jobs first (their tiles start early)
   std::vector<size_t> order;
   for (size_t i = 0; i < jobs.size(); ++i)
     if (jobs[i].plan->field == field) order.push_back(i);
@@ -105,7 +109,7 @@ ntt_status build_part(const std::vector<JobKey> &jobs, int field, Part *part) {
   uint32_t item = 0;
   for (uint32_t level = 0; level < max_passes; ++level) {
     for (size_t i : order) {
-      const JobKey &j = jobs[i];
+      const BatchJobRef &j = jobs[i];
       if (level >= j.plan->num_passes) continue;
       BatchSeg s{};
       int mode = 0;
@@ -126,6 +130,29 @@ ntt_status build_part(const std::vector<JobKey> &jobs, int field, Part *part) {
       segs.push_back(s);
     }
   }
+  *total_items = item;
+  return segs;
+}
+
+uint64_t batch_wait_limit_ns() { return g_wait_ns; }
+
+ntt_status batch_error_word(uint32_t **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_NO_DEVICE;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return device_err_word(dev, out);
+}
+
+}  // namespace gb300ntt
+
+namespace {
+
+// Build the segment table of the jobs of one field and upload it.
+ntt_status build_part(const std::vector<JobKey> &jobs, int field, Part *part) {
+  std::vector<BatchJobRef> refs;
+  for (const JobKey &j : jobs) refs.push_back(BatchJobRef{j.plan, j.kind, j.in, j.out});
+  uint32_t item = 0;
+  std::vector<BatchSeg> segs = build_segments(refs, field, &item);
   if (segs.empty()) return NTT_OK;
   if (g_stall) {
     // test hook: the last segment waits for one tile more than exists

@@ -196,8 +196,46 @@ cudaError_t set_all_pass_attrs() {
   return e;
 }
 
+template <int LOGS, int MODE>
+cudaError_t set_matrix_attr() {
+  return cudaFuncSetAttribute(ntt_matrix_pass_kernel<F, LOGS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              matrix_smem_bytes<LOGS>());
+}
+
+template <int LOGS>
+cudaError_t set_matrix_attrs() {
+  cudaError_t e = set_matrix_attr<LOGS, kModeInner>();
+  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirst>();
+  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirstPre>();
+  return e;
+}
+
+template <int LOGS>
+cudaError_t matrix_logs(int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
+  const int smem = matrix_smem_bytes<LOGS>();
+  switch (mode) {
+    case kModeInner: ntt_matrix_pass_kernel<F, LOGS, kModeInner><<<grid, kMatThreads, smem, st>>>(ma); break;
+    case kModeFirst: ntt_matrix_pass_kernel<F, LOGS, kModeFirst><<<grid, kMatThreads, smem, st>>>(ma); break;
+    case kModeFirstPre: ntt_matrix_pass_kernel<F, LOGS, kModeFirstPre><<<grid, kMatThreads, smem, st>>>(ma); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
+  switch (logs) {
+    case 1: return matrix_logs<1>(mode, ma, grid, st);
+    case 2: return matrix_logs<2>(mode, ma, grid, st);
+    case 3: return matrix_logs<3>(mode, ma, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t prepare() {
   cudaError_t e = set_all_pass_attrs<11>();
+  if (e == cudaSuccess) e = set_matrix_attrs<1>();
+  if (e == cudaSuccess) e = set_matrix_attrs<2>();
+  if (e == cudaSuccess) e = set_matrix_attrs<3>();
   if (e == cudaSuccess) e = set_all_pass_attrs<10>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
@@ -265,7 +303,7 @@ cudaError_t mul_vec(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, 
   return cudaGetLastError();
 }
 
-const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec, batch};
+const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec, batch, matrix_pass};
 
 }  // namespace
 }  // namespace gb300ntt

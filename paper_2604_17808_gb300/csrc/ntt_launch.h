@@ -9,6 +9,7 @@
 
 #include <cstdint>
 
+#include "ntt_matrix.cuh"
 #include "ntt_pass.cuh"
 
 namespace gb300ntt {
@@ -61,6 +62,8 @@ struct FieldLaunchers {
   cudaError_t (*mul_vec)(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, cudaStream_t st);
   // persistent batched kernel over the items of `b`
   cudaError_t (*batch)(const BatchLaunch &b, cudaStream_t st);
+  // one matrix-form pass (logs <= 3), `grid` persistent CTAs
+  cudaError_t (*matrix_pass)(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st);
 };
 
 const FieldLaunchers &launchers_bls12_381();

@@ -26,6 +26,7 @@
 #include "../../include/ntt_gb300.h"
 #include "host_field.h"
 #include "ntt_launch.h"
+#include "ntt_matrix.cuh"
 #include "ntt_plan.h"
 
 using namespace gb300ntt;
@@ -103,6 +104,14 @@ uint64_t pass_tiles(uint32_t log_n, uint32_t logs, uint32_t tl) {
 // the sub-transform fits in it, else the 2048-element tile.
 uint32_t default_tile_log(uint32_t logs) { return logs <= 10 ? 10 : 11; }
 
+// Balanced split of log_n into passes of at most max_log bits, larger first.
+std::vector<uint32_t> split_passes_max(uint32_t log_n, uint32_t max_log) {
+  const uint32_t P = (log_n + max_log - 1) / max_log;
+  std::vector<uint32_t> s(P, log_n / P);
+  for (uint32_t i = 0; i < log_n % P; ++i) s[i] += 1;
+  return s;
+}
+
 static ntt_status alloc_tab(ntt_plan p, uint4 **out, uint64_t elems) {
   void *ptr = nullptr;
   cudaError_t e = cudaMalloc(&ptr, elems * 32);
@@ -152,11 +161,11 @@ ntt_status build_coset_tables(ntt_plan p, const U256 &s, cudaStream_t st) {
   return NTT_OK;
 }
 
-ntt_status build_plan(ntt_plan p, cudaStream_t st) {
+ntt_status build_plan(ntt_plan p, cudaStream_t st, const std::vector<uint32_t> *forced_split) {
   const HostField F = host_field(p->field);
   const FieldLaunchers &L = launchers(p->field);
   const uint32_t log_n = p->log_n;
-  const std::vector<uint32_t> passes = split_passes(log_n);
+  const std::vector<uint32_t> passes = forced_split ? *forced_split : split_passes(log_n);
   p->num_passes = (uint32_t)passes.size();
   for (uint32_t j = 0; j < p->num_passes; ++j) {
     p->pass_log[j] = passes[j];
@@ -319,7 +328,7 @@ ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int c
   p->sm_count = prop.multiProcessorCount;
   cudaStream_t st = nullptr;
   ntt_status s = cuda_status(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  if (s == NTT_OK) s = build_plan(p, st);
+  if (s == NTT_OK) s = build_plan(p, st, nullptr);
   if (st) {
     const cudaError_t e = cudaStreamSynchronize(st);
     if (s == NTT_OK) s = cuda_status(e);
@@ -338,7 +347,10 @@ ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int c
 ntt_status ntt_plan_set_path(ntt_plan plan, ntt_path path) {
   if (!plan) return NTT_ERR_INVALID_ARG;
   if (path != NTT_PATH_AUTO && path != NTT_PATH_BUTTERFLY && path != NTT_PATH_MATRIX) return NTT_ERR_INVALID_ARG;
-  if (path == NTT_PATH_MATRIX && !matrix_path_available(plan)) return NTT_ERR_UNSUPPORTED;
+  if (path == NTT_PATH_MATRIX) {
+    if (!matrix_path_available(plan)) return NTT_ERR_UNSUPPORTED;
+    NTT_TRY(prepare_matrix_path(plan));
+  }
   plan->path = path;
   return NTT_OK;
 }
@@ -352,6 +364,7 @@ ntt_status ntt_plan_set_coset_shift(ntt_plan plan, const uint64_t shift[4]) {
   cudaStream_t st = nullptr;
   NTT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   ntt_status r = build_coset_tables(plan, s, st);
+  if (r == NTT_OK && plan->matrix && plan->matrix->nested) r = build_coset_tables(plan->matrix->nested, s, st);
   const cudaError_t e = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   if (r == NTT_OK) r = cuda_status(e);
@@ -488,6 +501,9 @@ ntt_status ntt_plan_poll_error(ntt_plan plan, uint32_t *code) {
   NTT_CUDA(cudaDeviceSynchronize());
   NTT_CUDA(cudaMemcpy(code, plan->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   NTT_CUDA(cudaMemset(plan->d_err, 0, sizeof(uint32_t)));
+  uint32_t mcode = 0;
+  NTT_TRY(matrix_poll_error(plan, &mcode));
+  if (!*code) *code = mcode;
   return NTT_OK;
 }
 

@@ -49,7 +49,20 @@ struct ntt_plan_s {
 
 namespace gb300ntt {
 
+// Resources of the matrix-form path (ntt_matrix.cu): a nested plan with
+// passes of at most 2^3 points and the byte matrices E per pass size.
+struct MatrixResources {
+  ntt_plan nested = nullptr;
+  uint4 *e[2][4] = {};      // [direction][log S] E matrices, B-operand layout
+  uint32_t *err = nullptr;  // device error word of matrix launches
+  uint32_t offset[9] = {};  // 2^18 * p
+};
+
 std::vector<uint32_t> split_passes(uint32_t log_n);
+std::vector<uint32_t> split_passes_max(uint32_t log_n, uint32_t max_log);
+// Build tables and scratch of plan p (fields device, field, log_n,
+// has_coset, sm_count set) for the given pass split (nullptr = default).
+ntt_status build_plan(ntt_plan p, cudaStream_t st, const std::vector<uint32_t> *forced_split);
 uint64_t pass_tiles(uint32_t log_n, uint32_t logs, uint32_t tl);
 ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
 ntt_status cuda_status(cudaError_t e);
@@ -60,13 +73,27 @@ ntt_status check_buffer(const void *ptr);
 cudaError_t timing_begin(ntt_plan p, int pass, cudaStream_t st);
 cudaError_t timing_end(ntt_plan p, cudaStream_t st);
 
+ntt_status build_coset_tables(ntt_plan p, const U256 &s, cudaStream_t st);
+
 // matrix (tensor-core) path, ntt_matrix.cu
 bool matrix_path_available(ntt_plan p);
+ntt_status prepare_matrix_path(ntt_plan p);
+ntt_status matrix_poll_error(ntt_plan p, uint32_t *code);
 ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
 uint32_t matrix_launches(ntt_plan p);
 void release_matrix_resources(ntt_plan p);
 
 // batched path, ntt_batch.cu
 void batch_forget_plan(ntt_plan plan);
+struct BatchSeg;
+struct BatchJobRef {
+  ntt_plan plan;
+  int32_t kind;
+  const void *in;
+  void *out;
+};
+std::vector<BatchSeg> build_segments(const std::vector<BatchJobRef> &jobs, int field, uint32_t *total_items);
+uint64_t batch_wait_limit_ns();
+ntt_status batch_error_word(uint32_t **out);
 
 }  // namespace gb300ntt

@@ -1,0 +1,123 @@
+"""GPU parity of the matrix-form path (every pass a tcgen05 tensor-core
+product of signed-byte digits with a precomputed byte matrix, then ByteMerge
+and Montgomery reduction) against the oracle, and path equivalence with the
+butterfly path (byte-identical outputs)."""
+
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ntt_oracle as O
+from ntt_synth import config_seed, uniform_elements
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2604_17808_gb300 import _native as N  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FIELDS = ["bls12_381_fr", "bn254_fr"]
+KINDS = ["forward", "inverse", "coset"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    N.load(build_if_missing=True)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.uint64)
+
+
+def matrix_plan(field, log_n, coset=True):
+    plan = N.ntt_plan_create(field, log_n, coset=coset)
+    N.ntt_plan_set_path(plan, "matrix")
+    return plan
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_matrix_path_all_small_sizes_and_kinds(field):
+    for log_n in range(1, 15):
+        plan = matrix_plan(field, log_n)
+        try:
+            desc = N.ntt_plan_describe(plan)
+            assert desc["path"] == 2 and desc["launches_per_transform"] == -(-log_n // 3)
+            for kind in KINDS:
+                x = uniform_elements(field, 1 << log_n, 40000 + log_n)
+                d_x = dev(x)
+                d_y = torch.empty_like(d_x)
+                N.ntt_execute(plan, kind, d_x, d_y)
+                assert np.array_equal(host(d_y), oracle.c_transform(field, kind, x)), (field, kind, log_n)
+            assert N.ntt_plan_poll_error(plan) == 0
+        finally:
+            N.ntt_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_matrix_path_adversarial_inputs(field):
+    # all p-1 and alternating maximal / zero limbs: the signed digits hit
+    # their extremes and every ByteMerge carry path is exercised
+    f = O.get_field(field)
+    log_n = 12
+    n = 1 << log_n
+    vals = [f.modulus - 1] * (n // 2) + [(f.modulus - 1) if i % 3 else 0 for i in range(n // 2)]
+    x = O.ints_to_limbs(vals)
+    plan = matrix_plan(field, log_n)
+    try:
+        for kind in KINDS:
+            d_x = dev(x)
+            d_y = torch.empty_like(d_x)
+            N.ntt_execute(plan, kind, d_x, d_y)
+            assert np.array_equal(host(d_y), oracle.c_transform(field, kind, x)), kind
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("kind", ["forward", "inverse"])
+def test_matrix_equals_butterfly_and_oracle_at_2_20(kind):
+    field, log_n = "bls12_381_fr", 20
+    x = uniform_elements(field, 1 << log_n, config_seed(2))
+    with open(os.path.join(HERE, "golden", "oracle_digests.json")) as fh:
+        want = [c for c in json.load(fh)["single"] if c["config"] == 2 and c["kind"] == kind][0]["output_sha256"]
+    plan = N.ntt_plan_create(field, log_n)
+    try:
+        d_x = dev(x)
+        d_b = torch.empty_like(d_x)
+        d_m = torch.empty_like(d_x)
+        N.ntt_execute(plan, kind, d_x, d_b)
+        N.ntt_plan_set_path(plan, "matrix")
+        N.ntt_execute(plan, kind, d_x, d_m)
+        assert torch.equal(d_b, d_m)
+        got = host(d_m)
+        assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == want
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
+def test_matrix_path_in_place_and_custom_shift():
+    field, log_n = "bn254_fr", 13
+    f = O.get_field(field)
+    s = 0xDEADBEEF12345678 % f.modulus
+    x = uniform_elements(field, 1 << log_n, 41000)
+    plan = matrix_plan(field, log_n)
+    try:
+        N.ntt_plan_set_coset_shift(plan, s)
+        d = dev(x)
+        N.ntt_execute(plan, "coset", d, d)
+        assert np.array_equal(host(d), oracle.c_transform(field, "coset", x, shift=s))
+    finally:
+        N.ntt_plan_destroy(plan)
