@@ -29,6 +29,7 @@
 
 #include <cstdint>
 
+#include "../../include/ntt_gb300.h"
 #include "fp256.cuh"
 #include "ntt_pass.cuh"
 
