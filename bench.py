@@ -307,24 +307,98 @@ def measure_batched(torch, N, stream, reps: int) -> dict:
             N.ntt_plan_destroy(p)
 
 
-def measure_e2e(torch, N, plan, x_host: np.ndarray, steps: int, stream) -> dict:
+def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int = 12, log_max: int = 24,
+                    seed: int = 0x5EED0005) -> dict:
+    """Poisson arrivals of mixed forward/inverse/coset requests over both
+    fields, log2 n uniform on {log_min..log_max}, through the serving runtime
+    (host buffers in, host buffers out).  Per rate: p50/p99 latency
+    (finish - arrive) and elements/s over the run."""
+    import random
+
+    server = N.ntt_server_create(memory_budget_bytes=64 << 30, min_log_n=log_min, max_log_n=log_max,
+                                 max_inflight=3, max_batch_jobs=64)
+    try:
+        # one pinned input and output buffer per (field, size), reused by every request
+        bufs = {}
+        for fi, field in enumerate(("bls12_381_fr", "bn254_fr")):
+            for ln in range(log_min, log_max + 1):
+                x = uniform_elements(field, 1 << ln, seed + 100 * fi + ln)
+                h_in = torch.from_numpy(x.view(np.int64)).pin_memory()
+                bufs[(field, ln)] = (h_in, torch.empty_like(h_in).pin_memory())
+        out = []
+        rng = random.Random(seed)
+        for rate in rates:
+            n_jobs = max(min_jobs, int(rate * seconds))
+            tickets = []
+            elements = 0
+            t_next = time.perf_counter()
+            for _ in range(n_jobs):
+                t_next += rng.expovariate(rate)
+                while time.perf_counter() < t_next:
+                    pass
+                field = rng.choice(("bls12_381_fr", "bn254_fr"))
+                kind = rng.choice(("forward", "inverse", "coset"))
+                ln = rng.randint(log_min, log_max)
+                h_in, h_out = bufs[(field, ln)]
+                tickets.append(N.ntt_server_submit(server, field, kind, ln, h_in, h_out))
+                elements += 1 << ln
+            lat, first, last = [], None, None
+            for t in tickets:
+                N.ntt_server_wait(server, t, 600.0)
+                a, _, f = N.ntt_server_request_times(server, t)
+                lat.append(f - a)
+                first = a if first is None else min(first, a)
+                last = f if last is None else max(last, f)
+                N.ntt_server_release(server, t)
+            lat.sort()
+            out.append({"rate_per_s": rate, "jobs": n_jobs, "elements": elements,
+                        "elements_per_s": elements / (last - first),
+                        "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
+                        "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)})
+        stats = N.ntt_server_get_stats(server)
+        return {"workload": f"Poisson arrivals, kinds forward/inverse/coset, fields BLS12-381/BN254, "
+                            f"log2 n uniform on {{{log_min}..{log_max}}}, 64 GiB budget, 3 streams",
+                "rates": out, "batches": stats["batches"], "peak_device_bytes": stats["peak_device_bytes"],
+                "resident_bytes": stats["resident_bytes"]}
+    finally:
+        N.ntt_server_destroy(server)
+
+
+def measure_e2e(torch, N, x_host: np.ndarray, steps: int, log_n: int) -> dict:
+    """End to end through the public host-buffer call: every step copies its
+    input from pinned host memory, runs forward then inverse, and copies the
+    result back (ntt_transform_host_async); steps alternate over two streams
+    (separate plans, device buffers and host buffers) so that one step's
+    copies overlap the other's kernels.  Wall-clock time over all steps."""
     n = x_host.shape[0]
-    h_in = torch.from_numpy(x_host.view(np.int64)).pin_memory()
-    h_mid = torch.empty_like(h_in).pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
-    d_work = torch.empty(h_in.shape, dtype=torch.int64, device="cuda")
+    lanes = []
     for _ in range(2):
-        N.ntt_transform_host(plan, "forward", h_in, h_mid, d_work, stream)
-        N.ntt_transform_host(plan, "inverse", h_mid, h_out, d_work, stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        N.ntt_transform_host(plan, "forward", h_in, h_mid, d_work, stream)
-        N.ntt_transform_host(plan, "inverse", h_mid, h_out, d_work, stream)
-    dt = time.perf_counter() - t0
-    ok = bool(torch.equal(h_out, h_in))
+        plan = N.ntt_plan_create(FIELD, log_n)
+        h_in = torch.from_numpy(x_host.view(np.int64).copy()).pin_memory()
+        lanes.append({"plan": plan, "stream": torch.cuda.Stream(), "h_in": h_in,
+                      "h_mid": torch.empty_like(h_in).pin_memory(), "h_out": torch.empty_like(h_in).pin_memory(),
+                      "d_work": torch.empty(h_in.shape, dtype=torch.int64, device="cuda")})
+
+    def step(ln):
+        N.ntt_transform_host_async(ln["plan"], "forward", ln["h_in"], ln["h_mid"], ln["d_work"], ln["stream"])
+        N.ntt_transform_host_async(ln["plan"], "inverse", ln["h_mid"], ln["h_out"], ln["d_work"], ln["stream"])
+
+    try:
+        for i in range(4):
+            step(lanes[i % 2])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            step(lanes[i % 2])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ok = all(bool(torch.equal(ln["h_out"], ln["h_in"])) for ln in lanes)
+    finally:
+        for ln in lanes:
+            N.ntt_plan_destroy(ln["plan"])
     return {"value": 2 * n * steps / dt, "unit": UNIT, "h2d_bytes_per_step": 2 * 32 * n,
-            "d2h_bytes_per_step": 2 * 32 * n, "round_trip_exact": ok}
+            "d2h_bytes_per_step": 2 * 32 * n, "round_trip_exact": ok,
+            "how": "ntt_transform_host_async, pinned host buffers, 2 streams, wall clock"}
 
 
 def cpu_baseline(x: np.ndarray, budget_s: float = 12.0) -> dict:
@@ -361,7 +435,7 @@ def run_ours(args) -> None:
     plan = N.ntt_plan_create(FIELD, log_n)
     desc = N.ntt_plan_describe(plan)
     host_inputs = [uniform_elements(FIELD, n, config_seed(2, 1000 * rank + r) if r else config_seed(2))
-                   for r in range(ROTATE)]
+                   for r in range(args.rotate)]
     bufs = []
     for h in host_inputs:
         x = to_dev(torch, h)
@@ -418,10 +492,11 @@ def run_ours(args) -> None:
     cpu = None
     matrix = measure_matrix(torch, N, stream, bufs, max(3, args.steps // 5), log_n)
     if rank == 0:
-        e2e = measure_e2e(torch, N, plan, host_inputs[0], max(3, args.steps // 4), stream)
+        e2e = measure_e2e(torch, N, host_inputs[0], max(8, args.steps // 2), log_n)
         if not args.quick:
             secondary = {"n_2_24_forward": measure_2_24(torch, N, stream, steps=max(3, args.steps // 4)),
-                         "batched": measure_batched(torch, N, stream, reps=5)}
+                         "batched": measure_batched(torch, N, stream, reps=5),
+                         "serving": measure_serving(torch, N, rates=(100, 1000, 5000), seconds=0.5, min_jobs=40)}
         if world == 1 and not args.no_cpu:
             cpu = cpu_baseline(host_inputs[0])
     N.ntt_plan_destroy(plan)
@@ -443,8 +518,9 @@ def run_ours(args) -> None:
         "data": "synthetic (uniform field elements from seed, SplitMix64)",
         "config": {"workload": f"BLS12-381 Fr NTT n=2^{log_n}, forward+inverse per step, butterfly path "
                                f"(passes {desc['pass_log']})",
-                   "field": FIELD, "log_n": log_n, "transforms_per_step": 2, "per_rank_vectors": ROTATE,
-                   "l2": L2_NOTE, "parallelism": f"replicas x{world}"},
+                   "field": FIELD, "log_n": log_n, "transforms_per_step": 2, "per_rank_vectors": args.rotate,
+                   "l2": L2_NOTE if args.rotate == ROTATE and log_n == LOG_N else
+                   f"{args.rotate} rotating 2^{log_n} vectors", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T IMAD/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": f"ntt_pass_kernel pass {dom} (S=2^{desc['pass_log'][dom]})",
@@ -515,6 +591,18 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_serving_sweep(args) -> None:
+    """--serving: the full sweep (>= 10 s or 2000 jobs per rate), one JSON line."""
+    import torch
+
+    from paper_2604_17808_gb300 import _native as N
+
+    torch.cuda.set_device(0)
+    N.load(build_if_missing=True)
+    res = measure_serving(torch, N, rates=(100, 300, 1000, 3000, 5000), seconds=10.0, min_jobs=2000)
+    print(json.dumps({"metric": "serving p50/p99 latency and elements/s", "serving": res}), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -524,11 +612,16 @@ def main() -> None:
     ap.add_argument("--log-n", type=int, default=LOG_N)
     ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
+    ap.add_argument("--rotate", type=int, default=ROTATE,
+                    help="distinct input vectors the steps rotate over (default 8: larger than L2 at 2^20)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.serving:
+        run_serving_sweep(args)
     else:
         run_ours(args)
 

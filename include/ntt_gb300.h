@@ -135,6 +135,17 @@ ntt_status ntt_transform_host(ntt_plan plan, ntt_kind kind, const void *h_in, vo
                               void *d_work, ntt_stream stream);
 
 /*
+ * Asynchronous form of ntt_transform_host: enqueues the host-to-device copy,
+ * the in-place transform of d_work and the device-to-host copy on `stream`
+ * and returns without synchronising.  h_in, h_out and d_work must stay
+ * valid (and h_in unmodified) until the stream has passed this work; with
+ * page-locked host buffers, transforms on different streams overlap their
+ * copies with each other's kernels.
+ */
+ntt_status ntt_transform_host_async(ntt_plan plan, ntt_kind kind, const void *h_in, void *h_out, void *d_work,
+                                    ntt_stream stream);
+
+/*
  * Read back the plan's structure: number of passes, the log2 size of each
  * pass's sub-transforms (up to 4), and the number of kernel launches one
  * transform makes.
@@ -161,6 +172,30 @@ ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out);
  */
 ntt_status ntt_plan_read_table(ntt_plan plan, ntt_kind kind, uint32_t pass, uint32_t table,
                                uint64_t first, uint64_t count, void *h_out);
+
+/*
+ * Autotuner: time candidate configurations of this plan's transform on the
+ * device and keep the fastest -- butterfly-path pass splits (balanced splits
+ * for every maximum pass size 2^4..2^11, in both orders) x tile shapes (1024-
+ * or 2048-element tiles), and the matrix path.  Each candidate runs one
+ * untimed and `reps` timed forward transforms (reps = 0: 3) on scratch
+ * buffers it allocates.  The plan's tables are rebuilt for the winner;
+ * cached batched job lists that use the plan are dropped.  The choice is
+ * remembered for (GPU, field, log_n): later ntt_plan_create calls in this
+ * process use it, and when the environment variable NTT_TUNE_CACHE names a
+ * file the choices are also written there and read by later processes.
+ * Synchronous; takes tens to hundreds of milliseconds.  result may be NULL.
+ */
+typedef struct ntt_tune_result {
+    uint32_t path;            /* ntt_path chosen */
+    uint32_t num_passes;      /* butterfly passes (the matrix path has its own split) */
+    uint32_t pass_log[4];
+    uint32_t tile_log[4];     /* log2 of each pass's tile (10 or 11) */
+    uint32_t candidates;
+    double best_ms;           /* forward transform, winner */
+    double default_ms;        /* forward transform, configuration before tuning */
+} ntt_tune_result;
+ntt_status ntt_plan_autotune(ntt_plan plan, uint32_t reps, ntt_tune_result *result);
 
 /*
  * Batched submission (the paper batches NTTs to fill its matrix units,

@@ -53,6 +53,12 @@ class ServerStats(ctypes.Structure):
                 ("peak_device_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_uint32), ("num_passes", ctypes.c_uint32), ("pass_log", ctypes.c_uint32 * 4),
+                ("tile_log", ctypes.c_uint32 * 4), ("candidates", ctypes.c_uint32), ("best_ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double)]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("kind", ctypes.c_int32), ("in_", ctypes.c_void_p),
                 ("out", ctypes.c_void_p)]
@@ -73,9 +79,11 @@ _SIGS = {
     "ntt_coset_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ntt_execute": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "ntt_transform_host": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "ntt_transform_host_async": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "ntt_plan_describe": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc)]),
     "ntt_plan_read_table": (ctypes.c_int, [_VP, ctypes.c_int, _U32, _U32, _U64, _U64, _VP]),
     "ntt_batch_submit": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP]),
+    "ntt_plan_autotune": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(TuneResult)]),
     "ntt_plan_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
     "ntt_batch_poll_error": (ctypes.c_int, [ctypes.POINTER(_U32)]),
     "ntt_batch_set_wait_limit": (ctypes.c_int, [_U64]),
@@ -204,6 +212,11 @@ def ntt_transform_host(plan: int, kind, h_in, h_out, d_work, stream=None) -> Non
            "ntt_transform_host")
 
 
+def ntt_transform_host_async(plan: int, kind, h_in, h_out, d_work, stream=None) -> None:
+    _check(load().ntt_transform_host_async(plan, _kind(kind), _ptr(h_in), _ptr(h_out), _ptr(d_work),
+                                           _stream(stream)), "ntt_transform_host_async")
+
+
 def ntt_plan_describe(plan: int) -> dict:
     d = PlanDesc()
     _check(load().ntt_plan_describe(plan, ctypes.byref(d)), "ntt_plan_describe")
@@ -215,6 +228,15 @@ def ntt_plan_describe(plan: int) -> dict:
 def ntt_plan_read_table(plan: int, kind, pass_index: int, table: int, first: int, count: int, h_out) -> None:
     _check(load().ntt_plan_read_table(plan, _kind(kind), pass_index, table, first, count, _ptr(h_out)),
            "ntt_plan_read_table")
+
+
+def ntt_plan_autotune(plan: int, reps: int = 3) -> dict:
+    r = TuneResult()
+    _check(load().ntt_plan_autotune(plan, int(reps), ctypes.byref(r)), "ntt_plan_autotune")
+    n = r.num_passes
+    return {"path": ["auto", "butterfly", "matrix"][r.path], "num_passes": n,
+            "pass_log": list(r.pass_log)[: min(n, 4)], "tile_log": list(r.tile_log)[: min(n, 4)],
+            "candidates": r.candidates, "best_ms": r.best_ms, "default_ms": r.default_ms}
 
 
 def ntt_batch_submit(jobs, stream=None) -> None:

@@ -51,6 +51,8 @@ struct FieldBn254Fr {
 
 static_assert(FieldBls12381Fr::P0 * (0u - FieldBls12381Fr::NP) == 1u, "NP");
 static_assert(FieldBn254Fr::P0 * (0u - FieldBn254Fr::NP) == 1u, "NP");
+static_assert(FieldBls12381Fr::P0 == 1u && FieldBls12381Fr::P1 == 0xffffffffu && FieldBls12381Fr::NP == 0xffffffffu,
+              "the BLS12-381 reduction rows rely on r = 2^64 - 2^32 + 1 mod 2^64");
 
 // ------------------------------------------------------------------ helpers
 
@@ -92,8 +94,11 @@ __device__ __forceinline__ void row_odd(uint32_t t[9], const uint32_t a[8], uint
 }
 
 // Same two chains with the modulus p (immediates) as the multi-limb operand.
+// For BLS12-381 Fr the two low limbs are p0 = 1 and p1 = 2^32 - 1 (r = ... +
+// 2^64 - 2^32 + 1), so m*p0 = m and m*p1 = (m - [m != 0]) * 2^32 + (-m mod
+// 2^32): those two products become additions (see row_*_p_bls below).
 template <class F>
-__device__ __forceinline__ void row_even_p(uint32_t t[9], uint32_t m) {
+__device__ __forceinline__ void row_even_p_generic(uint32_t t[9], uint32_t m) {
   asm("mad.lo.cc.u32  %0, %9, %10, %0;\n\t"
       "madc.hi.cc.u32 %1, %9, %10, %1;\n\t"
       "madc.lo.cc.u32 %2, %9, %11, %2;\n\t"
@@ -109,7 +114,7 @@ __device__ __forceinline__ void row_even_p(uint32_t t[9], uint32_t m) {
 }
 
 template <class F>
-__device__ __forceinline__ void row_odd_p(uint32_t t[9], uint32_t m) {
+__device__ __forceinline__ void row_odd_p_generic(uint32_t t[9], uint32_t m) {
   asm("mad.lo.cc.u32  %0, %8, %9,  %0;\n\t"
       "madc.hi.cc.u32 %1, %8, %9,  %1;\n\t"
       "madc.lo.cc.u32 %2, %8, %10, %2;\n\t"
@@ -120,6 +125,59 @@ __device__ __forceinline__ void row_odd_p(uint32_t t[9], uint32_t m) {
       "madc.hi.u32    %7, %8, %12, %7;"
       : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8])
       : "r"(m), "n"(F::P1), "n"(F::P3), "n"(F::P5), "n"(F::P7));
+}
+
+// BLS12-381 Fr: even chain with m*p0 = m (no multiply).
+template <class F>
+__device__ __forceinline__ void row_even_p_bls(uint32_t t[9], uint32_t m) {
+  asm("add.cc.u32     %0, %0, %9;\n\t"
+      "addc.cc.u32    %1, %1, 0;\n\t"
+      "madc.lo.cc.u32 %2, %9, %10, %2;\n\t"
+      "madc.hi.cc.u32 %3, %9, %10, %3;\n\t"
+      "madc.lo.cc.u32 %4, %9, %11, %4;\n\t"
+      "madc.hi.cc.u32 %5, %9, %11, %5;\n\t"
+      "madc.lo.cc.u32 %6, %9, %12, %6;\n\t"
+      "madc.hi.cc.u32 %7, %9, %12, %7;\n\t"
+      "addc.u32       %8, %8, 0;"
+      : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+        "+r"(t[8])
+      : "r"(m), "n"(F::P2), "n"(F::P4), "n"(F::P6));
+}
+
+// BLS12-381 Fr: odd chain with m*p1 = (m - [m != 0]) * 2^32 + (-m).
+template <class F>
+__device__ __forceinline__ void row_odd_p_bls(uint32_t t[9], uint32_t m) {
+  const uint32_t lo1 = 0u - m;
+  const uint32_t hi1 = m - (m != 0u ? 1u : 0u);
+  asm("add.cc.u32     %0, %0, %9;\n\t"
+      "addc.cc.u32    %1, %1, %10;\n\t"
+      "madc.lo.cc.u32 %2, %8, %11, %2;\n\t"
+      "madc.hi.cc.u32 %3, %8, %11, %3;\n\t"
+      "madc.lo.cc.u32 %4, %8, %12, %4;\n\t"
+      "madc.hi.cc.u32 %5, %8, %12, %5;\n\t"
+      "madc.lo.cc.u32 %6, %8, %13, %6;\n\t"
+      "madc.hi.u32    %7, %8, %13, %7;"
+      : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8])
+      : "r"(m), "r"(lo1), "r"(hi1), "n"(F::P3), "n"(F::P5), "n"(F::P7));
+}
+
+template <class F>
+__device__ __forceinline__ void row_even_p(uint32_t t[9], uint32_t m) {
+  if constexpr (F::kId == 0) row_even_p_bls<F>(t, m);
+  else row_even_p_generic<F>(t, m);
+}
+
+template <class F>
+__device__ __forceinline__ void row_odd_p(uint32_t t[9], uint32_t m) {
+  if constexpr (F::kId == 0) row_odd_p_bls<F>(t, m);
+  else row_odd_p_generic<F>(t, m);
+}
+
+// m = t0 * (-p^-1 mod 2^32); for BLS12-381 Fr p0 = 1, so m = -t0.
+template <class F>
+__device__ __forceinline__ uint32_t mont_m(uint32_t t0) {
+  if constexpr (F::kId == 0) return 0u - t0;
+  else return t0 * F::NP;
 }
 
 // r = t - p if t >= p else t   (t < 2p).
@@ -155,7 +213,7 @@ __device__ __forceinline__ void mont_mul(uint32_t r[8], const uint32_t a[8], con
   for (int i = 0; i < 8; ++i) {
     row_even(t, a, b[i]);
     row_odd(t, a, b[i]);
-    const uint32_t m = t[0] * F::NP;
+    const uint32_t m = mont_m<F>(t[0]);
     row_even_p<F>(t, m);
     row_odd_p<F>(t, m);
     // t[0] is now zero: divide by 2^32.

@@ -116,7 +116,7 @@ __device__ __forceinline__ void merge_reduce(uint32_t y[8], const uint32_t acc_b
   // Montgomery reduction of the 9-limb value (< 2^274 < p * 2^256)
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const uint32_t m = t[0] * F::NP;
+    const uint32_t m = mont_m<F>(t[0]);
     row_even_p<F>(t, m);
     row_odd_p<F>(t, m);
 #pragma unroll
@@ -285,15 +285,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
         const uint32_t m = e / S, k = e % S;
         const uint64_t d = d0 + m;
         if (d < a.num_sub) {
-          uint64_t rest = d, rev = 0;
-#pragma unroll
-          for (int j = 3; j >= 0; --j) {
-            if (j < (int)a.num_digits) {
-              const uint64_t nj = rest & ((1ull << a.digit_log[j]) - 1);
-              rest >>= a.digit_log[j];
-              rev |= nj << a.digit_shift[j];
-            }
-          }
+          const uint64_t rev = reverse_digits(a, d);
           uint32_t v[8];
           tile_load(v, reinterpret_cast<const uint4 *>(sA), m * S + k);
           fe_store_global(a.dst, (rev << LOGS) | k, v);

@@ -81,6 +81,10 @@ enum PassMode : int {
   kModeFirstPre = 2,  // pass 0 with a per-n_0 input multiplier table [S]
 };
 
+// At most this many passes per transform (the matrix path splits 2^28 into
+// ten passes of at most 2^3 points).
+constexpr int kMaxPasses = 12;
+
 struct PassArgs {
   const uint4 *src;      // input elements (2 x uint4 each)
   uint4 *dst;            // output elements
@@ -89,9 +93,23 @@ struct PassArgs {
   uint64_t num_sub;      // number of sub-transforms in the pass, N / S
   uint32_t log_mp;       // inner: log2 Mp; first: log2(N / S)
   uint32_t num_digits;   // first: P - 1 untransformed digits to reverse
-  uint32_t digit_log[4];    // first: log2 S_j of digit j (j = 1..P-1) at index j-1
-  uint32_t digit_shift[4];  // first: log2(S_1 ... S_{j-1}) at index j-1
+  uint8_t digit_log[kMaxPasses];    // first: log2 S_j of digit j (j = 1..P-1) at index j-1
+  uint8_t digit_shift[kMaxPasses];  // first: log2(S_1 ... S_{j-1}) at index j-1
 };
+
+// Output row of pass 0 for untransformed digits d (their significance reversed).
+__device__ __forceinline__ uint64_t reverse_digits(const PassArgs &a, uint64_t d) {
+  uint64_t rest = d, rev = 0;
+#pragma unroll
+  for (int j = kMaxPasses - 1; j >= 0; --j) {
+    if (j < (int)a.num_digits) {
+      const uint64_t nj = rest & ((1ull << a.digit_log[j]) - 1);
+      rest >>= a.digit_log[j];
+      rev |= nj << a.digit_shift[j];
+    }
+  }
+  return rev;
+}
 
 // ------------------------------------------------------------- swizzle
 // Chunk c = 2e + h (16-byte half h of tile element e) is stored at
@@ -315,16 +333,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
       const uint32_t dl = e >> LOGS, k = e & (S - 1);
       const uint64_t d = d0 + dl;
       if (d < a.num_sub) {
-        // reverse the significance of the untransformed digits of d
-        uint64_t rest = d, rev = 0;
-#pragma unroll
-        for (int j = 3; j >= 0; --j) {
-          if (j < (int)a.num_digits) {
-            const uint64_t nj = rest & ((1ull << a.digit_log[j]) - 1);
-            rest >>= a.digit_log[j];
-            rev |= nj << a.digit_shift[j];
-          }
-        }
+        const uint64_t rev = reverse_digits(a, d);
         uint32_t v[8];
         tile_load(v, smem, (dl << LOGS) | bit_reverse_local<LOGS>(k));
         fe_store_global(a.dst, (rev << LOGS) | k, v);

@@ -166,6 +166,7 @@ ntt_status build_plan(ntt_plan p, cudaStream_t st, const std::vector<uint32_t> *
   const FieldLaunchers &L = launchers(p->field);
   const uint32_t log_n = p->log_n;
   const std::vector<uint32_t> passes = forced_split ? *forced_split : split_passes(log_n);
+  if (passes.empty() || passes.size() > (size_t)kMaxPasses) return NTT_ERR_UNSUPPORTED;
   p->num_passes = (uint32_t)passes.size();
   for (uint32_t j = 0; j < p->num_passes; ++j) {
     p->pass_log[j] = passes[j];
@@ -232,8 +233,8 @@ void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j
     a->num_digits = P - 1;
     uint32_t shift = 0;
     for (uint32_t d = 1; d < P; ++d) {
-      a->digit_log[d - 1] = p->pass_log[d];
-      a->digit_shift[d - 1] = shift;
+      a->digit_log[d - 1] = (uint8_t)p->pass_log[d];
+      a->digit_shift[d - 1] = (uint8_t)shift;
       shift += p->pass_log[d];
     }
     a->mul = p->pre[kind];
@@ -334,6 +335,10 @@ ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int c
     if (s == NTT_OK) s = cuda_status(e);
     cudaStreamDestroy(st);
   }
+  if (s == NTT_OK) {
+    TuneChoice tc;
+    if (tune_lookup(dev, (int)field, log_n, &tc)) s = tune_apply(p, tc);
+  }
   if (s == NTT_OK) s = cuda_status(cudaMalloc(&p->d_err, sizeof(uint32_t)));
   if (s == NTT_OK) s = cuda_status(cudaMemset(p->d_err, 0, sizeof(uint32_t)));
   if (s != NTT_OK) {
@@ -413,6 +418,18 @@ ntt_status ntt_transform_host(ntt_plan plan, ntt_kind kind, const void *h_in, vo
   NTT_TRY(ntt_execute(plan, kind, d_work, d_work, stream));
   NTT_CUDA(cudaMemcpyAsync(h_out, d_work, bytes, cudaMemcpyDeviceToHost, st));
   NTT_CUDA(cudaStreamSynchronize(st));
+  return NTT_OK;
+}
+
+ntt_status ntt_transform_host_async(ntt_plan plan, ntt_kind kind, const void *h_in, void *h_out, void *d_work,
+                                    ntt_stream stream) {
+  if (!plan || !h_in || !h_out) return NTT_ERR_INVALID_ARG;
+  NTT_TRY(check_buffer(d_work));
+  const size_t bytes = (size_t)32 << plan->log_n;
+  cudaStream_t st = (cudaStream_t)stream;
+  NTT_CUDA(cudaMemcpyAsync(d_work, h_in, bytes, cudaMemcpyHostToDevice, st));
+  NTT_TRY(ntt_execute(plan, kind, d_work, d_work, stream));
+  NTT_CUDA(cudaMemcpyAsync(h_out, d_work, bytes, cudaMemcpyDeviceToHost, st));
   return NTT_OK;
 }
 

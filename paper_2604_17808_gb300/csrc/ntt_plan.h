@@ -9,6 +9,7 @@
 
 #include "../../include/ntt_gb300.h"
 #include "host_field.h"
+#include "ntt_pass.cuh"
 
 namespace gb300ntt {
 
@@ -26,15 +27,15 @@ struct ntt_plan_s {
   ntt_path path = NTT_PATH_AUTO;
   int sm_count = 0;
   uint32_t num_passes = 0;
-  uint32_t pass_log[4] = {0, 0, 0, 0};
-  uint32_t pass_tl[4] = {11, 11, 11, 11};  // log2 tile size of each pass (10 or 11)
+  uint32_t pass_log[gb300ntt::kMaxPasses] = {};
+  uint32_t pass_tl[gb300ntt::kMaxPasses] = {};  // log2 tile size of each pass (10 or 11)
   uint32_t launches = 0;
   gb300ntt::U256 omega{}, omega_inv{}, coset_shift{};
   // device tables, Montgomery form, 32 bytes per entry
   uint4 *dft_tw[2][12] = {};     // [direction][log S]: omega_S^(+-i), i < S/2
-  uint4 *tw[3][4] = {};          // [kind][pass >= 1]: inter-pass multipliers [S_j][Mp]
+  uint4 *tw[3][gb300ntt::kMaxPasses] = {};  // [kind][pass >= 1]: inter-pass multipliers [S_j][Mp]
   uint4 *pre[3] = {};            // [kind]: pass-0 multipliers [S_0] (coset; single-pass inverse)
-  uint4 *fac_coset[4] = {};      // [pass >= 1]: s^(n N / M_j), n < S_j
+  uint4 *fac_coset[gb300ntt::kMaxPasses] = {};  // [pass >= 1]: s^(n N / M_j), n < S_j
   uint4 *scratch = nullptr;      // N elements (in-place transforms with > 1 pass)
   uint32_t *d_err = nullptr;     // device error word
   std::vector<void *> allocations;
@@ -82,6 +83,17 @@ ntt_status matrix_poll_error(ntt_plan p, uint32_t *code);
 ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
 uint32_t matrix_launches(ntt_plan p);
 void release_matrix_resources(ntt_plan p);
+
+// autotuner, ntt_tune.cu
+struct TuneChoice {
+  int path = 1;                  // NTT_PATH_BUTTERFLY or NTT_PATH_MATRIX
+  std::vector<uint32_t> split;   // butterfly pass sizes (log2)
+  uint32_t tile_log = 10;        // 10 or 11 (butterfly)
+  double ms = 0;
+};
+
+bool tune_lookup(int dev, int field, uint32_t log_n, TuneChoice *out);
+ntt_status tune_apply(ntt_plan p, const TuneChoice &c);
 
 // batched path, ntt_batch.cu
 void batch_forget_plan(ntt_plan plan);

@@ -287,7 +287,14 @@ def test_transform_host_round_trip():
         h_out = torch.empty_like(h_in).pin_memory()
         d_work = torch.empty(h_in.shape, dtype=torch.int64, device="cuda")
         N.ntt_transform_host(plan, "forward", h_in, h_out, d_work)
-        assert np.array_equal(h_out.numpy().view(np.uint64), oracle.c_transform(field, "forward", x))
+        want = oracle.c_transform(field, "forward", x)
+        assert np.array_equal(h_out.numpy().view(np.uint64), want)
+        # asynchronous form on a side stream
+        h_out2 = torch.zeros_like(h_in).pin_memory()
+        s = torch.cuda.Stream()
+        N.ntt_transform_host_async(plan, "forward", h_in, h_out2, d_work, s)
+        s.synchronize()
+        assert np.array_equal(h_out2.numpy().view(np.uint64), want)
     finally:
         N.ntt_plan_destroy(plan)
 

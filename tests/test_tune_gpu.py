@@ -1,0 +1,72 @@
+"""GPU tests of the autotuner: a tuned plan still computes the exact
+transform (all kinds, custom coset shift kept), the choice is remembered for
+later plans of the same (field, size) and written to NTT_TUNE_CACHE."""
+
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ntt_oracle as O
+from ntt_synth import uniform_elements
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2604_17808_gb300 import _native as N  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.uint64)
+
+
+def test_autotune_keeps_results_exact_and_remembers_the_choice(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("NTT_TUNE_CACHE", str(cache))
+    N.load(build_if_missing=True)
+    field, log_n = "bls12_381_fr", 15
+    f = O.get_field(field)
+    s = 0x123456789 % f.modulus
+    x = uniform_elements(field, 1 << log_n, 60000)
+    plan = N.ntt_plan_create(field, log_n, coset=True)
+    try:
+        N.ntt_plan_set_coset_shift(plan, s)
+        res = N.ntt_plan_autotune(plan, reps=2)
+        assert res["candidates"] >= 4
+        assert res["best_ms"] > 0 and res["best_ms"] <= res["default_ms"] * 1.5
+        desc = N.ntt_plan_describe(plan)
+        if res["path"] == "butterfly":
+            assert desc["pass_log"] == res["pass_log"]
+        for kind in ("forward", "inverse", "coset"):
+            d_x = dev(x)
+            d_y = torch.empty_like(d_x)
+            N.ntt_execute(plan, kind, d_x, d_y)
+            want = oracle.c_transform(field, kind, x, shift=s if kind == "coset" else None)
+            assert np.array_equal(host(d_y), want), kind
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+    assert cache.exists() and f"|0|{log_n} " in cache.read_text()
+    # a new plan of the same field and size starts from the tuned choice
+    plan2 = N.ntt_plan_create(field, log_n)
+    try:
+        d2 = N.ntt_plan_describe(plan2)
+        assert d2["path"] == {"butterfly": 1, "matrix": 2}[res["path"]]
+        if res["path"] == "butterfly":
+            assert d2["pass_log"] == res["pass_log"]
+        d_x = dev(x)
+        d_y = torch.empty_like(d_x)
+        N.ntt_forward(plan2, d_x, d_y)
+        assert np.array_equal(host(d_y), oracle.c_transform(field, "forward", x))
+    finally:
+        N.ntt_plan_destroy(plan2)
