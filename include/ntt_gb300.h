@@ -228,6 +228,35 @@ typedef struct ntt_job {
 } ntt_job;
 ntt_status ntt_batch_submit(const ntt_job *jobs, size_t n, ntt_stream stream);
 
+/*
+ * ntt_batch_submit without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they submit work -- code that runs while a stream is being captured
+ * into a CUDA graph (cudaMalloc is not a capturable operation and
+ * synchronises the device), and services that reserve all their device
+ * memory up front and must not allocate once they are serving.
+ * ntt_batch_submit allocates a work-item table and counters per new job list
+ * and captures a CUDA graph; this call instead runs the same persistent
+ * batched kernel with its table and counters in one fixed-size array that
+ * the library holds in device memory (about 55 KB on every GPU that loads
+ * the library, until the process exits).  It calls no cudaMalloc, cudaFree
+ * or other allocating routine; the caller passes the plans (created
+ * beforehand) and the input and output buffers, as for ntt_batch_submit.
+ *
+ * Limits: at most 64 jobs per call (NTT_ERR_UNSUPPORTED beyond); same job
+ * rules as ntt_batch_submit (in != out, butterfly-path plans, no overlap).
+ * d_status: device pointer to one uint32_t (4-byte aligned) set to 0 at the
+ * start of the call and to NTT_ERR_TIMEOUT if a device wait of the kernel
+ * ran out; may be NULL.
+ *
+ * The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call on a device shares the one array, which keeps the
+ * last call's contents (the call clears the counters it needs): calls whose
+ * work overlaps on the GPU race -- order them on one stream.
+ */
+ntt_status ntt_batch_submit_static(const ntt_job *jobs, size_t n, uint32_t *d_status, ntt_stream stream);
+
 /* First error recorded by batched kernels on the current device since the
  * last poll (0 = none), then cleared.  Synchronises the device. */
 ntt_status ntt_batch_poll_error(uint32_t *code);

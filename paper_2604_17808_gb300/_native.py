@@ -85,6 +85,7 @@ _SIGS = {
     "ntt_batch_submit": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP]),
     "ntt_plan_autotune": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(TuneResult)]),
     "ntt_plan_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
+    "ntt_batch_submit_static": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP, _VP]),
     "ntt_batch_poll_error": (ctypes.c_int, [ctypes.POINTER(_U32)]),
     "ntt_batch_set_wait_limit": (ctypes.c_int, [_U64]),
     "ntt_batch_debug_stall": (ctypes.c_int, [ctypes.c_int]),
@@ -246,6 +247,15 @@ def ntt_batch_submit(jobs, stream=None) -> None:
     for i, (plan, kind, d_in, d_out) in enumerate(jobs):
         arr[i] = Job(plan, _kind(kind), _ptr(d_in), _ptr(d_out))
     _check(load().ntt_batch_submit(arr, len(jobs), _stream(stream)), "ntt_batch_submit")
+
+
+def ntt_batch_submit_static(jobs, d_status=None, stream=None) -> None:
+    """jobs: iterable of (plan, kind, d_in, d_out); d_status: device uint32 or None."""
+    jobs = list(jobs)
+    arr = (Job * max(1, len(jobs)))()
+    for i, (plan, kind, d_in, d_out) in enumerate(jobs):
+        arr[i] = Job(plan, _kind(kind), _ptr(d_in), _ptr(d_out))
+    _check(load().ntt_batch_submit_static(arr, len(jobs), _ptr(d_status), _stream(stream)), "ntt_batch_submit_static")
 
 
 def ntt_batch_poll_error() -> int:
