@@ -79,6 +79,36 @@ def imad_peak_tops() -> float:
     return SMS * IMAD_PER_CLK_PER_SM * mhz * 1e6 / 1e12
 
 
+KERNEL_SOURCES = ("paper_2604_17808_gb300/csrc/fp256.cuh", "paper_2604_17808_gb300/csrc/ntt_pass.cuh",
+                  "paper_2604_17808_gb300/csrc/ntt_kernels.inl")
+PROFILE_2_20 = os.path.join(ROOT, "profiles", "ntt_pass_kernel_bls12_381_2_20.md")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag: str) -> int | None:
+    """DRAM bytes per launch of `kernel_tag` from the committed ncu summary,
+    if it was captured from the current kernel sources (else None)."""
+    try:
+        text = open(PROFILE_2_20).read()
+    except OSError:
+        return None
+    src = None
+    traffic = None
+    for line in text.splitlines():
+        if line.startswith("source_sha256:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith(f"traffic_bytes_per_launch[{kernel_tag}]:"):
+            traffic = int(line.split(":", 1)[1].strip())
+    return traffic if src == kernel_source_hash() else None
+
+
 def pass_modmuls(log_n: int, pass_log: list[int], j: int, has_multiplier: bool) -> int:
     n = 1 << log_n
     return (n // 2) * pass_log[j] + (n if has_multiplier else 0)
@@ -258,6 +288,31 @@ def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
                 "round_trip_exact": same, "device_error": N.ntt_plan_poll_error(plan)}
     finally:
         N.ntt_plan_destroy(plan)
+
+
+def measure_modmul(torch, N, stream, count: int = 1 << 22, reps: int = 64) -> dict:
+    """Montgomery products per second: per-thread carry chains (the library's
+    form) vs 8 lanes per element with warp-shuffle carries."""
+    x = to_dev(torch, uniform_elements(FIELD, count, 77))
+    y = to_dev(torch, uniform_elements(FIELD, count, 78))
+    res = {}
+    outs = []
+    for variant, name in ((0, "thread_carry_chains"), (1, "warp_shuffle_carries")):
+        z = torch.empty_like(x)
+        N.ntt_field_mont_mul_rep(FIELD, x, y, z, count, reps, variant, stream)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        N.ntt_field_mont_mul_rep(FIELD, x, y, z, count, reps, variant, stream)
+        stop.record(stream)
+        stop.synchronize()
+        ms = start.elapsed_time(stop)
+        res[name] = {"ms": round(ms, 4), "modmul_per_s": count * reps / (ms * 1e-3),
+                     "imad_frac_alg": count * reps * IMAD_PER_MODMUL / (ms * 1e-3) / 1e12 / imad_peak_tops()}
+        outs.append(z)
+    res["identical"] = bool(torch.equal(outs[0], outs[1]))
+    res["workload"] = f"{count} BLS12-381 elements x {reps} dependent Montgomery products"
+    return res
 
 
 def measure_batched(torch, N, stream, reps: int) -> dict:
@@ -496,6 +551,7 @@ def run_ours(args) -> None:
         if not args.quick:
             secondary = {"n_2_24_forward": measure_2_24(torch, N, stream, steps=max(3, args.steps // 4)),
                          "batched": measure_batched(torch, N, stream, reps=5),
+                         "modmul": measure_modmul(torch, N, stream),
                          "serving": measure_serving(torch, N, rates=(100, 1000, 5000), seconds=0.5, min_jobs=40)}
         if world == 1 and not args.no_cpu:
             cpu = cpu_baseline(host_inputs[0])
@@ -522,7 +578,11 @@ def run_ours(args) -> None:
                    "l2": L2_NOTE if args.rotate == ROTATE and log_n == LOG_N else
                    f"{args.rotate} rotating 2^{log_n} vectors", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T IMAD/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic(f"pass{dom}") if log_n == LOG_N else None,
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, ncu --set full "
+                                     "(cold cache), only if captured from the current kernel sources",
+                     "kernel_source_sha256": kernel_source_hash(),
                      "kernel": f"ntt_pass_kernel pass {dom} (S=2^{desc['pass_log'][dom]})",
                      "avg_launch_ms": avg_ms,
                      "peak_note": "152 SMs x 64 IMAD/clk x 2070 MHz (unit counts and maximum clock)"},

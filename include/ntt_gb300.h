@@ -359,6 +359,18 @@ ntt_status ntt_server_destroy(ntt_server server);
 ntt_status ntt_field_mont_mul(ntt_field field, const void *d_a, const void *d_b, void *d_out, uint64_t count,
                               ntt_stream stream);
 
+/*
+ * Diagnostic / throughput probe of the field multiplication: out[i] =
+ * a[i] * (b[i] * 2^-256)^reps mod M, i.e. `reps` dependent Montgomery
+ * products per element.  variant 0: one thread per element, carry chains in
+ * registers (what every kernel of this library uses); variant 1: eight lanes
+ * per element, one 32-bit limb each, carries moved between lanes by warp
+ * shuffles (the warp-cooperative form).  Same results; the two exist to
+ * measure the difference.  count elements, reps >= 1.  Stream-ordered.
+ */
+ntt_status ntt_field_mont_mul_rep(ntt_field field, const void *d_a, const void *d_b, void *d_out, uint64_t count,
+                                  uint32_t reps, int variant, ntt_stream stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *ntt_status_string(ntt_status status);
 

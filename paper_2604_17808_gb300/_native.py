@@ -91,6 +91,7 @@ _SIGS = {
     "ntt_batch_debug_stall": (ctypes.c_int, [ctypes.c_int]),
     "ntt_batch_cache_clear": (ctypes.c_int, []),
     "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
+    "ntt_field_mont_mul_rep": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _U32, ctypes.c_int, _VP]),
     "ntt_plan_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ntt_plan_read_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U64)]),
     "ntt_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)]),
@@ -343,6 +344,11 @@ def ntt_server_get_stats(server: int) -> dict:
 
 def ntt_server_destroy(server: int) -> None:
     _check(load().ntt_server_destroy(server), "ntt_server_destroy")
+
+
+def ntt_field_mont_mul_rep(field, d_a, d_b, d_out, count: int, reps: int, variant: int, stream=None) -> None:
+    _check(load().ntt_field_mont_mul_rep(_field(field), _ptr(d_a), _ptr(d_b), _ptr(d_out), int(count), int(reps),
+                                         int(variant), _stream(stream)), "ntt_field_mont_mul_rep")
 
 
 def ntt_status_string(status: int) -> str:

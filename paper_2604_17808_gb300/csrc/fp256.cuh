@@ -276,6 +276,60 @@ __device__ __forceinline__ void sub_mod(uint32_t r[8], const uint32_t a[8], cons
   for (int j = 0; j < 8; ++j) r[j] = d[j];
 }
 
+// ------------------------------------------- warp-cooperative variant
+// The same CIOS Montgomery product with one element spread over 8 lanes
+// (lane j of each aligned group of 8 holds limb j): every lane does the two
+// 32x32 products of its limb per row, the high halves move one lane up by
+// warp shuffle, the reduction factor m is broadcast from lane 0, and the
+// running value is shifted one lane down per row.  Columns are kept in 64-bit
+// accumulators (carries deferred); after the 8 rows the carries are
+// propagated lane to lane, and the final comparison / subtraction of p uses
+// a carry-lookahead on warp ballots.  Kept as a measured alternative to the
+// per-thread carry chains (mont_mul), which have no shuffle traffic.
+template <class F>
+__device__ __forceinline__ uint32_t mont_mul_coop(uint32_t a_j, uint32_t b_j, uint32_t j) {
+  constexpr uint32_t kFull = 0xffffffffu;
+  const uint32_t p_j = j == 0 ? F::P0 : j == 1 ? F::P1 : j == 2 ? F::P2 : j == 3 ? F::P3
+                     : j == 4 ? F::P4 : j == 5 ? F::P5 : j == 6 ? F::P6 : F::P7;
+  uint64_t acc = 0, top = 0;  // top: column 8, kept by lane 7
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t bi = __shfl_sync(kFull, b_j, i, 8);
+    const uint64_t pr = (uint64_t)a_j * bi;
+    const uint32_t hi_in = __shfl_up_sync(kFull, (uint32_t)(pr >> 32), 1, 8);
+    acc += (uint64_t)(uint32_t)pr + (j ? hi_in : 0u);
+    if (j == 7) top += pr >> 32;
+    const uint32_t m = __shfl_sync(kFull, mont_m<F>((uint32_t)acc), 0, 8);
+    const uint64_t pm = (uint64_t)p_j * m;
+    const uint32_t hm_in = __shfl_up_sync(kFull, (uint32_t)(pm >> 32), 1, 8);
+    acc += (uint64_t)(uint32_t)pm + (j ? hm_in : 0u);
+    if (j == 7) top += pm >> 32;
+    // column 0 is now 0 mod 2^32: its high part carries into column 1
+    const uint32_t c0 = __shfl_sync(kFull, (uint32_t)(acc >> 32), 0, 8);  // columns stay < 2^38
+    if (j == 1) acc += c0;
+    // divide by 2^32: every column moves one lane down
+    const uint32_t nx_lo = __shfl_down_sync(kFull, (uint32_t)acc, 1, 8);
+    const uint32_t nx_hi = __shfl_down_sync(kFull, (uint32_t)(acc >> 32), 1, 8);
+    acc = j == 7 ? top : ((uint64_t)nx_hi << 32 | nx_lo);
+    if (j == 7) top = 0;
+  }
+  // propagate the deferred carries (each column < 2^38)
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t c = __shfl_up_sync(kFull, (uint32_t)(acc >> 32), 1, 8);
+    acc = (acc & 0xffffffffull) + (j ? c : 0u);
+  }
+  const uint32_t t = (uint32_t)acc;  // t < 2p
+  // t - p if t >= p: borrow lookahead over the group's 8 lanes
+  const uint32_t base = (threadIdx.x & 31u) & ~7u;
+  const uint32_t G = (__ballot_sync(kFull, t < p_j) >> base) & 0xffu;   // generates a borrow
+  const uint32_t P = (__ballot_sync(kFull, t == p_j) >> base) & 0xffu;  // propagates one
+  const uint32_t x = G | P, sum = x + G;
+  const uint32_t borrow_in = ((sum ^ x ^ G) >> j) & 1u;
+  const bool ge = ((sum >> 8) & 1u) == 0;  // no borrow out of the top limb
+  return ge ? t - p_j - borrow_in : t;
+}
+
 __device__ __forceinline__ void fe_copy(uint32_t r[8], const uint32_t a[8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) r[j] = a[j];

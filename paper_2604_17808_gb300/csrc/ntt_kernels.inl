@@ -163,6 +163,34 @@ cudaError_t batch(const BatchLaunch &b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// out[i] = a[i] * (b[i] * 2^-256)^reps: `reps` dependent Montgomery products
+// per element, per-thread carry chains (variant 0) or 8 lanes per element
+// with shuffle carries (variant 1).
+__global__ void mul_rep_kernel(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, uint32_t reps) {
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x[8], y[8];
+    fe_load_global(x, a, idx);
+    fe_load_global(y, b, idx);
+    for (uint32_t r = 0; r < reps; ++r) mont_mul<F>(x, x, y);
+    fe_store_global(out, idx, x);
+  }
+}
+
+__global__ void mul_rep_coop_kernel(uint32_t *out, const uint32_t *a, const uint32_t *b, uint64_t count,
+                                    uint32_t reps) {
+  // 8 lanes per element; the grid covers every element exactly (no early exit
+  // of part of a warp: the shuffles need all 32 lanes)
+  const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint32_t j = threadIdx.x & 7u;
+  const uint64_t elem = gid >> 3;
+  const bool live = elem < count;
+  uint32_t x = live ? a[elem * 8 + j] : 0u;
+  const uint32_t y = live ? b[elem * 8 + j] : 0u;
+  for (uint32_t r = 0; r < reps; ++r) x = mont_mul_coop<F>(x, y, j);
+  if (live) out[elem * 8 + j] = x;
+}
+
 template <int LOGS, int MODE, int TL>
 cudaError_t set_pass_attr() {
   return cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -303,7 +331,19 @@ cudaError_t mul_vec(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, 
   return cudaGetLastError();
 }
 
-const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec, batch, matrix_pass};
+cudaError_t mul_rep(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, uint32_t reps, int variant,
+                    cudaStream_t st) {
+  if (variant == 0) {
+    mul_rep_kernel<<<grid_for(count), 256, 0, st>>>(out, a, b, count, reps);
+  } else {
+    const uint64_t threads = count * 8;
+    mul_rep_coop_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+        (uint32_t *)out, (const uint32_t *)a, (const uint32_t *)b, count, reps);
+  }
+  return cudaGetLastError();
+}
+
+const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec, batch, mul_rep, matrix_pass};
 
 }  // namespace
 }  // namespace gb300ntt

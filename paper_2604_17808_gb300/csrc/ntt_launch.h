@@ -62,6 +62,9 @@ struct FieldLaunchers {
   cudaError_t (*mul_vec)(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, cudaStream_t st);
   // persistent batched kernel over the items of `b`
   cudaError_t (*batch)(const BatchLaunch &b, cudaStream_t st);
+  // out[i] = a[i] * (b[i] 2^-256)^reps; variant 0 per-thread chains, 1 warp-cooperative
+  cudaError_t (*mul_rep)(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, uint32_t reps, int variant,
+                         cudaStream_t st);
   // one matrix-form pass (logs <= 3), `grid` persistent CTAs
   cudaError_t (*matrix_pass)(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st);
 };

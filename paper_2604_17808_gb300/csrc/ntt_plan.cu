@@ -535,6 +535,19 @@ ntt_status ntt_field_mont_mul(ntt_field field, const void *d_a, const void *d_b,
       launchers((int)field).mul_vec((uint4 *)d_out, (const uint4 *)d_a, (const uint4 *)d_b, count, (cudaStream_t)stream));
 }
 
+ntt_status ntt_field_mont_mul_rep(ntt_field field, const void *d_a, const void *d_b, void *d_out, uint64_t count,
+                                  uint32_t reps, int variant, ntt_stream stream) {
+  if (field != NTT_FIELD_BLS12_381_FR && field != NTT_FIELD_BN254_FR) return NTT_ERR_INVALID_ARG;
+  if (reps == 0 || (variant != 0 && variant != 1)) return NTT_ERR_INVALID_ARG;
+  if (count == 0) return NTT_OK;
+  if (count > (1ull << 28)) return NTT_ERR_UNSUPPORTED;
+  NTT_TRY(check_buffer(d_a));
+  NTT_TRY(check_buffer(d_b));
+  NTT_TRY(check_buffer(d_out));
+  return cuda_status(launchers((int)field).mul_rep((uint4 *)d_out, (const uint4 *)d_a, (const uint4 *)d_b, count, reps,
+                                                   variant, (cudaStream_t)stream));
+}
+
 const char *ntt_status_string(ntt_status status) {
   switch (status) {
     case NTT_OK: return "NTT_OK";

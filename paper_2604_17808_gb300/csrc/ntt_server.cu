@@ -23,6 +23,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <set>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -49,6 +50,69 @@ struct Request {
   bool done = false;
 };
 
+// Buddy allocator over one device arena.  Request buffers are 32 * 2^log_n
+// bytes, so blocks of order k (32 * 2^k bytes) split and coalesce exactly;
+// the arena is reserved once at server creation, so serving never calls
+// cudaMalloc / cudaFree (cudaFree synchronises the whole device).
+class BuddyArena {
+ public:
+  ntt_status init(uint64_t bytes, uint32_t max_order) {
+    max_order_ = max_order;
+    const uint64_t top = kUnit << max_order;
+    const uint64_t n_top = bytes / top;
+    if (n_top == 0) return NTT_ERR_BUDGET;
+    if (cudaMalloc(&base_, n_top * top) != cudaSuccess) {
+      cudaGetLastError();
+      base_ = nullptr;
+      return NTT_ERR_OOM;
+    }
+    capacity_ = n_top * top;
+    free_.assign(max_order + 1, {});
+    for (uint64_t i = 0; i < n_top; ++i) free_[max_order].insert(i << max_order);
+    return NTT_OK;
+  }
+  ~BuddyArena() {
+    if (base_) cudaFree(base_);
+  }
+  // nullptr when no block of this order can be formed right now
+  void *alloc(uint32_t order) {
+    uint32_t o = order;
+    while (o <= max_order_ && free_[o].empty()) ++o;
+    if (o > max_order_) return nullptr;
+    uint64_t off = *free_[o].begin();
+    free_[o].erase(free_[o].begin());
+    while (o > order) {  // split, keep the lower half
+      --o;
+      free_[o].insert(off + (1ull << o));
+    }
+    used_ += kUnit << order;
+    peak_ = std::max(peak_, used_);
+    return static_cast<char *>(base_) + off * kUnit;
+  }
+  void release(void *p, uint32_t order) {
+    uint64_t off = (uint64_t)(static_cast<char *>(p) - static_cast<char *>(base_)) / kUnit;
+    used_ -= kUnit << order;
+    while (order < max_order_) {
+      const uint64_t buddy = off ^ (1ull << order);
+      auto it = free_[order].find(buddy);
+      if (it == free_[order].end()) break;
+      free_[order].erase(it);
+      off = std::min(off, buddy);
+      ++order;
+    }
+    free_[order].insert(off);
+  }
+  uint64_t capacity() const { return capacity_; }
+  uint64_t peak() const { return peak_; }
+
+ private:
+  static constexpr uint64_t kUnit = 32;
+  void *base_ = nullptr;
+  uint32_t max_order_ = 0;
+  uint64_t capacity_ = 0, used_ = 0, peak_ = 0;
+  std::vector<std::set<uint64_t>> free_;
+};
+
 // One in-flight batch slot: a stream, its segment staging and device tables.
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -70,11 +134,7 @@ struct ntt_server_s {
   Clock::time_point t0;
   ntt_plan plans[2][32] = {};
   uint64_t resident_bytes = 0;
-  // device buffer pool: free lists by size (bytes); every byte counts
-  std::map<uint64_t, std::vector<void *>> free_bufs;
-  uint64_t pool_bytes = 0;    // allocated (in use + cached)
-  uint64_t in_use_bytes = 0;
-  uint64_t peak_bytes = 0;
+  BuddyArena arena;            // request buffers (budget - resident tables)
   std::mutex mu;
   std::condition_variable cv;
   std::deque<uint64_t> queue;  // tickets waiting for admission
@@ -95,47 +155,6 @@ double now_s(const ntt_server_s *s) {
 }
 
 uint64_t job_bytes(uint32_t log_n) { return 32ull << log_n; }
-
-// Reserve one device buffer of `bytes` from the pool within the budget
-// (caller holds the lock).  Returns nullptr if the budget does not allow it.
-void *pool_get(ntt_server_s *s, uint64_t bytes) {
-  auto it = s->free_bufs.find(bytes);
-  if (it != s->free_bufs.end() && !it->second.empty()) {
-    void *p = it->second.back();
-    it->second.pop_back();
-    s->in_use_bytes += bytes;
-    return p;
-  }
-  const uint64_t budget = s->cfg.memory_budget_bytes;
-  // evict cached buffers of other sizes until the new one fits
-  while (s->resident_bytes + s->pool_bytes + bytes > budget) {
-    bool freed = false;
-    for (auto &kv : s->free_bufs) {
-      if (!kv.second.empty()) {
-        cudaFree(kv.second.back());
-        kv.second.pop_back();
-        s->pool_bytes -= kv.first;
-        freed = true;
-        break;
-      }
-    }
-    if (!freed) return nullptr;
-  }
-  void *p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  s->pool_bytes += bytes;
-  s->in_use_bytes += bytes;
-  s->peak_bytes = std::max(s->peak_bytes, s->resident_bytes + s->pool_bytes);
-  return p;
-}
-
-void pool_put(ntt_server_s *s, void *p, uint64_t bytes) {
-  s->free_bufs[bytes].push_back(p);
-  s->in_use_bytes -= bytes;
-}
 
 void CUDART_CB slot_done(void *arg) {
   static_cast<Slot *>(arg)->complete.store(1, std::memory_order_release);
@@ -208,8 +227,8 @@ void worker_loop(ntt_server_s *s) {
           Request &r = s->reqs[tk];
           r.finish = t;
           r.done = true;
-          pool_put(s, r.d_in, job_bytes(r.log_n));
-          pool_put(s, r.d_out, job_bytes(r.log_n));
+          s->arena.release(r.d_in, r.log_n);
+          s->arena.release(r.d_out, r.log_n);
           r.d_in = r.d_out = nullptr;
           s->completed += 1;
         }
@@ -222,12 +241,11 @@ void worker_loop(ntt_server_s *s) {
     // admit waiting requests while memory allows (in arrival order)
     while (!s->queue.empty()) {
       Request &r = s->reqs[s->queue.front()];
-      const uint64_t b = job_bytes(r.log_n);
-      void *in = pool_get(s, b);
+      void *in = s->arena.alloc(r.log_n);
       if (!in) break;
-      void *out = pool_get(s, b);
+      void *out = s->arena.alloc(r.log_n);
       if (!out) {
-        pool_put(s, in, b);
+        s->arena.release(in, r.log_n);
         break;
       }
       r.d_in = in;
@@ -275,8 +293,6 @@ void destroy_server(ntt_server_s *s) {
     }
     delete sl;
   }
-  for (auto &kv : s->free_bufs)
-    for (void *p : kv.second) cudaFree(p);
   for (auto &row : s->plans)
     for (ntt_plan p : row)
       if (p) ntt_plan_destroy(p);
@@ -331,6 +347,13 @@ ntt_status ntt_server_create(const ntt_server_config *cfg, ntt_server *out) {
   if (s->resident_bytes + 2 * job_bytes(c.max_log_n) > c.memory_budget_bytes) {
     destroy_server(s);
     return NTT_ERR_BUDGET;
+  }
+  {
+    const ntt_status st = s->arena.init(c.memory_budget_bytes - s->resident_bytes, c.max_log_n);
+    if (st != NTT_OK) {
+      destroy_server(s);
+      return st;
+    }
   }
   // in-flight slots: worst-case segment count per field = jobs * passes
   const uint32_t cap = c.max_batch_jobs * 4;
@@ -430,7 +453,7 @@ ntt_status ntt_server_get_stats(ntt_server s, ntt_server_stats *out) {
   out->batches = s->batches;
   out->queued = s->queue.size() + s->admitted.size();
   out->resident_bytes = s->resident_bytes;
-  out->peak_device_bytes = s->peak_bytes;
+  out->peak_device_bytes = s->resident_bytes + s->arena.peak();
   out->budget_bytes = s->cfg.memory_budget_bytes;
   return NTT_OK;
 }

@@ -96,6 +96,24 @@ def test_field_mont_mul_edge_operands(field):
     assert got == want
 
 
+@pytest.mark.parametrize("field", FIELDS)
+def test_field_mont_mul_variants_agree_with_python(field):
+    # per-thread carry chains (0) and 8-lane warp-shuffle carries (1)
+    f = O.get_field(field)
+    p = f.modulus
+    rng = random.Random(12)
+    a = [0, 1, p - 1, p - 2, 2**32 - 1, 2**224 + 5, (p + 1) // 2] + [rng.randrange(p) for _ in range(249)]
+    b = [p - 1, 1, p - 1, 2**64 + 1, 0, 3, (p - 1) // 2] + [rng.randrange(p) for _ in range(249)]
+    rinv = pow(2**256, -1, p)
+    d_a, d_b = dev(O.ints_to_limbs(a)), dev(O.ints_to_limbs(b))
+    for reps in (1, 2, 7):
+        want = [x * pow(y * rinv % p, reps, p) % p for x, y in zip(a, b)]
+        for variant in (0, 1):
+            d_c = torch.empty_like(d_a)
+            N.ntt_field_mont_mul_rep(field, d_a, d_b, d_c, len(a), reps, variant)
+            assert O.limbs_to_ints(host(d_c)) == want, (reps, variant)
+
+
 # ------------------------------------------------------ all small sizes
 
 
@@ -273,6 +291,31 @@ def test_bls12_381_2_24_forward_sampled_outputs_and_round_trip():
     finally:
         N.ntt_plan_destroy(plan)
     _horner_spot_checks(field, x, y, "forward", samples=2, seed=4)
+
+
+def test_maximum_size_2_28_round_trip_and_sampled_outputs():
+    # 2^28 points (BN254 Fr's 2-adicity, the largest size the library takes):
+    # 8 GiB per vector.  The oracle evaluates sampled outputs one by one.
+    field, log_n = "bn254_fr", 28
+    n = 1 << log_n
+    x = uniform_elements(field, n, 0x5EED0100)
+    plan = N.ntt_plan_create(field, log_n)
+    try:
+        d_x = dev(x)
+        d_y = torch.empty_like(d_x)
+        N.ntt_forward(plan, d_x, d_y)
+        N.ntt_inverse(plan, d_y, d_y)  # in place
+        torch.cuda.synchronize()
+        assert torch.equal(d_y, d_x)
+        N.ntt_forward(plan, d_x, d_y)
+        f = O.get_field(field)
+        w = O.root_of_unity(f, n)
+        ks = [1, n - 1, 0x1234567]
+        got = O.limbs_to_ints(d_y[ks].cpu().numpy().view(np.uint64))
+        for k, v in zip(ks, got):
+            assert v == oracle.c_eval(field, x, pow(w, k, f.modulus)), k
+    finally:
+        N.ntt_plan_destroy(plan)
 
 
 # ------------------------------------------------------------ boundary
