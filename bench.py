@@ -28,7 +28,7 @@ Printed as ONE JSON line on rank 0, with
   * clocks: nvidia-smi samples taken during the timed region.
 
 ``--impl reference`` times the oracle instead (rank 0 only), the baseline
-the driver compares against.
+the comparison of the two arms uses.
 """
 
 from __future__ import annotations

@@ -2,7 +2,7 @@
  * ntt_gb300.h -- C ABI of the GB300 (sm_103a) 255-bit number-theoretic
  * transform library.
  *
- * The operation (MORPH, Sec. 2.3.1, "Number Theory Transformation"): for a
+ * The operation (MORPH, Sec. 2.3.1, the NTT definition): for a
  * vector x of N = 2^log_n elements of the prime field F_M,
  *
  *     forward:  X_k = sum_{n<N} x_n * omega_N^{k n}            mod M
@@ -85,8 +85,8 @@ typedef enum ntt_kind {
 
 typedef enum ntt_path {
     NTT_PATH_AUTO = 0,      /* the library's choice (butterfly passes) */
-    NTT_PATH_BUTTERFLY = 1, /* radix-2^k shared-memory butterfly passes on 32-bit IMAD (Fig. 4a) */
-    NTT_PATH_MATRIX = 2     /* matrix-form column DFT on tensor cores (Sec. 3.3.2, Alg. 2 ByteDecompose/Einsum/ByteMerge) */
+    NTT_PATH_BUTTERFLY = 1, /* radix-2^k shared-memory butterfly passes on 32-bit IMAD (Fig. 5a) */
+    NTT_PATH_MATRIX = 2     /* matrix-form column DFT on tensor cores (Sec. 3.3.2; Alg. 1 ByteDecompose/Einsum/ByteMerge) */
 } ntt_path;
 
 typedef struct ntt_plan_s *ntt_plan;

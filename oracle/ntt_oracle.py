@@ -6,7 +6,7 @@ CPU-baseline / reference arm of ``bench.py`` use it.  It shares no code with
 the CUDA library (``paper_2604_17808_gb300``): it has its own copy of the field
 moduli, its own arithmetic (Python big integers) and its own transform.
 
-What it computes (MORPH, Sec. 2.3.1 "Number Theory Transformation"):
+What it computes (MORPH, Sec. 2.3.1, the NTT definition):
 
     X_k = sum_{n=0}^{N-1} x_n * omega_N^{k n}  mod M,   k in [0, N)
 
@@ -29,7 +29,7 @@ Two evaluations of the definition are provided:
   * ``dft_direct``: the definition written out, O(N^2); used for tiny N.
   * ``ntt``: the textbook iterative radix-2 Cooley-Tukey evaluation (bit
     reversal, then log2 N butterfly stages; the paper's "butterfly NTT",
-    Sec. 2.3.3 and Fig. 4a), which reaches exactly the same integers.
+    Sec. 2.3.3 and Fig. 5a), which reaches exactly the same integers.
 
 The pins that tie this module to something other than itself live in
 ``tests/test_oracle_pins.py`` (a library NTT, closed forms, invariants,

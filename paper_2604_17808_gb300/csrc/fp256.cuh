@@ -1,6 +1,6 @@
 // fp256.cuh -- 255-bit prime-field arithmetic for sm_103a, 8 x 32-bit limbs.
 //
-// The paper's arithmetic baseline ("radix Mont", Sec. 2.3.2 and Tab. 2): a
+// The paper's arithmetic baseline ("radix Mont", Sec. 2.3.2 and Tab. 1): a
 // field element is D = 8 32-bit digits; a multiplication is an O(D^2) digit
 // product with carry propagation followed by an O(D^2) Montgomery reduction.
 // On a GPU the carry chains are native (mad.lo.cc / madc.hi.cc on the

@@ -1,9 +1,8 @@
 // ntt_batch.cu -- many independent transforms in one persistent launch.
 //
-// The paper batches NTTs to fill its matrix units ("NTT favors >= 128
-// batches", Sec. 4.4, Fig. 7).  On GB300 a single small transform leaves most
-// of the 152 SMs idle (a 2^14-point pass has 8 tiles), so a batch is run as
-// one persistent kernel per field: every (job, pass, tile) is an item in one
+// The paper batches NTTs to keep its matrix units busy (Sec. 4.4, Fig. 7).
+// On GB300 a single small transform leaves most of the 152 SMs idle (a
+// 2^14-point pass has 8 tiles), so a batch is run as one persistent kernel per field: every (job, pass, tile) is an item in one
 // queue ordered by pass level, CTAs (3 per SM) claim items with an atomic
 // counter, and an item of pass j waits (time-bounded) for the completion
 // counter of pass j-1 of its own job.  The segment table and counters of a

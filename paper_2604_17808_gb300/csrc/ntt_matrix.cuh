@@ -1,6 +1,6 @@
 // ntt_matrix.cuh -- matrix-form sub-transforms on the tcgen05 tensor cores.
 //
-// The paper's reformulation (Sec. 3.2.3-3.2.4, Alg. 2; Sec. 3.3.2, Fig. 4b-c):
+// The paper's reformulation (Sec. 3.2.3-3.2.4, Alg. 1; Sec. 3.3.2, Fig. 5b-c):
 // high-precision modular arithmetic becomes a low-precision matrix product
 // over byte limbs (ByteDecompose -> uint8 "Einsum" against a precomputed
 // byte matrix E -> ByteMerge), and the NTT's sub-transforms become matrix

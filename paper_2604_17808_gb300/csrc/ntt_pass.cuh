@@ -1,6 +1,6 @@
 // ntt_pass.cuh -- one pass of the multi-pass (four-/six-step) NTT on sm_103a.
 //
-// Decomposition (the paper's 3-step / 5-step NTT, Sec. 3.3.2, Fig. 4b-c and
+// Decomposition (the paper's 3-step / 5-step NTT, Sec. 3.3.2, Fig. 5b-c and
 // Eq. 1, in the standard Cooley-Tukey index map): N = S_0 * S_1 * ... *
 // S_{P-1}.  Write the input index as n = sum_j n_j * N / (S_0 ... S_j), so
 // digit n_0 has the largest stride.  Then

@@ -9,9 +9,8 @@
 //     s^(n * N/M) for the digit the pass transforms);
 //   * pass 0 multipliers for coset (s^(n N/S_0)) and, for single-pass
 //     plans, the inverse scale N^-1.
-// The MORPH paper keeps its twiddle matrices resident ("generated offline",
-// Fig. 4); on GB300 they are generated once per plan by kernels and stay in
-// HBM.
+// The paper precomputes its twiddle matrices (Fig. 5); here they are
+// generated once per plan by kernels and stay in HBM.
 #include <cuda_runtime.h>
 
 #include <algorithm>
