@@ -2,13 +2,13 @@
 //
 // The paper batches NTTs to keep its matrix units busy (Sec. 4.4, Fig. 7).
 // On GB300 a single small transform leaves most of the 152 SMs idle (a
-// 2^14-point pass has 8 tiles), so a batch is run as one persistent kernel per field: every (job, pass, tile) is an item in one
-// queue ordered by pass level, CTAs (3 per SM) claim items with an atomic
-// counter, and an item of pass j waits (time-bounded) for the completion
-// counter of pass j-1 of its own job.  The segment table and counters of a
-// job list are built once; the launch sequence (counter reset + kernels) is
-// captured into a CUDA graph and replayed on later submissions of the same
-// job list.
+// 2^14-point pass has 8 tiles), so a batch is run as one persistent kernel
+// per field: every (job, pass, tile) is an item in one queue ordered by pass
+// level, CTAs (3 per SM) claim items with an atomic counter, and an item of
+// pass j waits (time-bounded) for the completion counter of pass j-1 of its
+// own job.  The segment table and counters of a job list are built once; the
+// launch sequence (counter reset + kernels) is captured into a CUDA graph and
+// replayed on later submissions of the same job list.
 #include <cuda_runtime.h>
 
 #include <algorithm>
