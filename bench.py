@@ -290,6 +290,65 @@ def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
         N.ntt_plan_destroy(plan)
 
 
+def measure_quotient(torch, N, stream, reps: int, log_n: int = 20, blowup_log: int = 2) -> dict:
+    """A prover's quotient step: coset NTTs of A, B, C (degree < 2n, zero
+    padded) on the coset s<omega_m> of m = 4n points, the fused pointwise
+    quotient (a b - c) / (X^n - 1), and the coset inverse NTT (n = 2^20,
+    BLS12-381 Fr, shift 7).  Correctness of the chain is pinned by the GPU
+    tests (it returns Q exactly for C = A B - (X^n - 1) Q)."""
+    from ntt_synth import MODULI
+
+    p = MODULI[FIELD]
+    n, m = 1 << log_n, 1 << (log_n + blowup_log)
+    s = 7                                      # coset shift = generator
+    w_b = pow(7, (p - 1) >> blowup_log, p)     # primitive 2^blowup_log-th root
+    sn = pow(s, n, p)
+    z = [pow((sn * pow(w_b, j, p) - 1) % p, p - 2, p) for j in range(1 << blowup_log)]
+    plan = N.ntt_plan_create(FIELD, log_n + blowup_log, coset=True)
+    try:
+        ins = []
+        for i in range(3):
+            h = np.zeros((m, 4), dtype=np.uint64)
+            h[: 2 * n] = uniform_elements(FIELD, 2 * n, config_seed(2, 300 + i))
+            ins.append(to_dev(torch, h))
+        work = [torch.empty_like(ins[0]) for _ in range(3)]
+
+        def step():
+            for i in range(3):
+                N.ntt_coset_forward(plan, ins[i], work[i], stream)
+            N.ntt_pointwise_quotient(FIELD, work[0], work[1], work[2], z, work[0], m, stream)
+            N.ntt_coset_inverse(plan, work[0], work[0], stream)
+
+        step()
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        mid = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(reps):
+            step()
+        stop.record(stream)
+        stop.synchronize()
+        ms = start.elapsed_time(stop) / reps
+        # the fused pointwise kernel alone
+        start.record(stream)
+        for _ in range(reps):
+            N.ntt_pointwise_quotient(FIELD, work[0], work[1], work[2], z, work[1], m, stream)
+        mid.record(stream)
+        mid.synchronize()
+        q_ms = start.elapsed_time(mid) / reps
+        # two products and one reduction per element (2.5 modmul equivalents)
+        q_frac = 2.5 * m * IMAD_PER_MODMUL / (q_ms * 1e-3) / 1e12 / imad_peak_tops()
+        return {"workload": f"prover quotient step, BLS12-381 Fr, n=2^{log_n}, coset of m=2^{log_n + blowup_log} "
+                            "points: 3 coset NTTs + fused pointwise (a b - c)/Z_H + coset inverse NTT",
+                "ms": round(ms, 4), "coset_points_per_s": m / (ms * 1e-3),
+                "pointwise_ms": round(q_ms, 4), "pointwise_imad_frac": round(q_frac, 4),
+                "pointwise_hbm_gbs": round(4 * 32 * m / (q_ms * 1e-3) / 1e9, 1),
+                "device_error": N.ntt_plan_poll_error(plan)}
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
 def measure_modmul(torch, N, stream, count: int = 1 << 22, reps: int = 64) -> dict:
     """Montgomery products per second: per-thread carry chains (the library's
     form) vs 8 lanes per element with warp-shuffle carries."""
@@ -419,15 +478,16 @@ def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int
         N.ntt_server_destroy(server)
 
 
-def measure_e2e(torch, N, x_host: np.ndarray, steps: int, log_n: int) -> dict:
+def measure_e2e(torch, N, x_host: np.ndarray, steps: int, log_n: int, num_lanes: int = 4) -> dict:
     """End to end through the public host-buffer call: every step copies its
     input from pinned host memory, runs forward then inverse, and copies the
-    result back (ntt_transform_host_async); steps alternate over two streams
-    (separate plans, device buffers and host buffers) so that one step's
-    copies overlap the other's kernels.  Wall-clock time over all steps."""
+    result back (ntt_transform_host_async); steps rotate over `num_lanes`
+    streams (separate plans, device buffers and host buffers) so that some
+    steps' copies overlap other steps' kernels.  Wall-clock time over all
+    steps."""
     n = x_host.shape[0]
     lanes = []
-    for _ in range(2):
+    for _ in range(num_lanes):
         plan = N.ntt_plan_create(FIELD, log_n)
         h_in = torch.from_numpy(x_host.view(np.int64).copy()).pin_memory()
         lanes.append({"plan": plan, "stream": torch.cuda.Stream(), "h_in": h_in,
@@ -439,12 +499,12 @@ def measure_e2e(torch, N, x_host: np.ndarray, steps: int, log_n: int) -> dict:
         N.ntt_transform_host_async(ln["plan"], "inverse", ln["h_mid"], ln["h_out"], ln["d_work"], ln["stream"])
 
     try:
-        for i in range(4):
-            step(lanes[i % 2])
+        for i in range(2 * num_lanes):
+            step(lanes[i % num_lanes])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(steps):
-            step(lanes[i % 2])
+            step(lanes[i % num_lanes])
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         ok = all(bool(torch.equal(ln["h_out"], ln["h_in"])) for ln in lanes)
@@ -453,7 +513,7 @@ def measure_e2e(torch, N, x_host: np.ndarray, steps: int, log_n: int) -> dict:
             N.ntt_plan_destroy(ln["plan"])
     return {"value": 2 * n * steps / dt, "unit": UNIT, "h2d_bytes_per_step": 2 * 32 * n,
             "d2h_bytes_per_step": 2 * 32 * n, "round_trip_exact": ok,
-            "how": "ntt_transform_host_async, pinned host buffers, 2 streams, wall clock"}
+            "how": f"ntt_transform_host_async, pinned host buffers, {num_lanes} streams, wall clock"}
 
 
 def cpu_baseline(x: np.ndarray, budget_s: float = 12.0) -> dict:
@@ -552,6 +612,7 @@ def run_ours(args) -> None:
             secondary = {"n_2_24_forward": measure_2_24(torch, N, stream, steps=max(3, args.steps // 4)),
                          "batched": measure_batched(torch, N, stream, reps=5),
                          "modmul": measure_modmul(torch, N, stream),
+                         "quotient_step": measure_quotient(torch, N, stream, reps=5),
                          "serving": measure_serving(torch, N, rates=(100, 1000, 5000), seconds=0.5, min_jobs=40)}
         if world == 1 and not args.no_cpu:
             cpu = cpu_baseline(host_inputs[0])

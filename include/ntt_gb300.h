@@ -18,7 +18,8 @@
  * Data layout (every buffer, host or device): N elements, element i at byte
  * offset 32*i, each element four little-endian uint64 limbs (limb 0 least
  * significant), standard (not Montgomery) representation, canonical in
- * [0, M), natural order in and out.  Device buffers must be 16-byte aligned.
+ * [0, M), natural order in and out.  Device buffers must be 32-byte aligned
+ * (one element; the kernels move each element with one 256-bit access).
  *
  * Ownership: the caller owns every input and output buffer.  A plan owns its
  * device-resident twiddle tables and one scratch vector of N elements, all
@@ -80,7 +81,13 @@ typedef enum ntt_field {
 typedef enum ntt_kind {
     NTT_KIND_FORWARD = 0,
     NTT_KIND_INVERSE = 1,
-    NTT_KIND_COSET = 2      /* coset forward */
+    NTT_KIND_COSET = 2,     /* coset forward: X_k = sum_n x_n (s omega^k)^n */
+    NTT_KIND_COSET_INVERSE = 3 /* coset inverse: x_n = s^-n N^-1 sum_k X_k omega^-nk
+                                  (interpolation from the coset s<omega>; undoes
+                                  NTT_KIND_COSET).  Not in the paper, which states
+                                  the forward transform only (Sec. 2.3.1); it is the
+                                  prover step after pointwise work on coset
+                                  evaluations. */
 } ntt_kind;
 
 typedef enum ntt_path {
@@ -95,9 +102,9 @@ typedef struct ntt_plan_s *ntt_plan;
  * Create a plan for N = 2^log_n elements of `field` on the current CUDA
  * device.  Builds (on the device) the twiddle tables of the forward and the
  * inverse transform, and of the coset transform when `coset` is nonzero
- * (shift = the field's generator), and allocates the scratch vector.
- * Cost: a few milliseconds plus about (3 + coset) * 32 * N bytes of device
- * memory.  On success *out holds the plan; on failure *out is NULL.
+ * (shift = the field's generator) and its inverse, and allocates the scratch
+ * vector.  Cost: a few milliseconds plus about (3 + 2 * coset) * 32 * N bytes
+ * of device memory.  On success *out holds the plan; on failure *out is NULL.
  */
 ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int coset);
 
@@ -115,14 +122,17 @@ ntt_status ntt_plan_set_coset_shift(ntt_plan plan, const uint64_t shift[4]);
 ntt_status ntt_plan_destroy(ntt_plan plan);
 
 /*
- * The three transforms, device buffers, stream-ordered.  d_in and d_out hold
- * N elements each (layout above); d_in == d_out (in place) is allowed.
+ * The transforms, device buffers, stream-ordered.  d_in and d_out hold N
+ * elements each (layout above); d_in == d_out (in place) is allowed.  The
+ * two coset kinds need a plan created with coset != 0 (else
+ * NTT_ERR_INVALID_ARG).
  */
 ntt_status ntt_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream);
 ntt_status ntt_inverse(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream);
 ntt_status ntt_coset_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream);
+ntt_status ntt_coset_inverse(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream);
 
-/* Same as the three calls above, with the kind as an argument. */
+/* Same as the calls above, with the kind as an argument. */
 ntt_status ntt_execute(ntt_plan plan, ntt_kind kind, const void *d_in, void *d_out, ntt_stream stream);
 
 /*
@@ -167,7 +177,9 @@ ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out);
  * tables against an independent computation.  table: 0 = the DFT twiddles
  * omega_S^i (i < S/2) of pass `pass`'s sub-transform size S; 1 = the input
  * multipliers of pass `pass` (pass >= 1: omega_M^{n q} [times s^{...} and
- * N^-1 folded in], row-major [n][q]; pass 0: the coset / scale factors).
+ * N^-1 folded in], row-major [n][q]; pass 0: the coset / scale factors);
+ * 2 = the output multipliers s^-n (n < N) of the last pass of a coset
+ * inverse (kind NTT_KIND_COSET_INVERSE, pass = the last pass).
  * Synchronous.
  */
 ntt_status ntt_plan_read_table(ntt_plan plan, ntt_kind kind, uint32_t pass, uint32_t table,
@@ -348,6 +360,25 @@ ntt_status ntt_server_release(ntt_server server, uint64_t ticket);
 ntt_status ntt_server_get_stats(ntt_server server, ntt_server_stats *out);
 /* Finish every submitted request, then free the server. */
 ntt_status ntt_server_destroy(ntt_server server);
+
+/*
+ * Pointwise quotient of a prover on coset evaluations, fused into one kernel
+ * (one pass over the vectors: 3 reads, 1 write per element):
+ *   out[i] = (a[i] * b[i] - c[i]) * z[i mod z_len] mod M,  i < count.
+ * a, b, c, out: device vectors of `count` elements (layout above, canonical;
+ * out may alias an input).  h_z: z_len elements in HOST memory, standard
+ * form, canonical; z_len a power of two, 1..64.  The typical z is the
+ * inverse of the vanishing polynomial X^n - 1 of an n-point domain on a
+ * coset of 2^k n points, which takes 2^k values (z_len = 2^k).  The paper
+ * has no counterpart (its workload is the transform); this is the step
+ * between a prover's coset transforms and the coset inverse.
+ * Stream-ordered; h_z is read before the call returns (no device memory is
+ * allocated).  NTT_ERR_INVALID_ARG for a bad field, z_len, z value or
+ * buffer.
+ */
+ntt_status ntt_pointwise_quotient(ntt_field field, const void *d_a, const void *d_b, const void *d_c,
+                                  const uint64_t *h_z, uint32_t z_len, void *d_out, uint64_t count,
+                                  ntt_stream stream);
 
 /*
  * Diagnostic: element-wise Montgomery product of device vectors,

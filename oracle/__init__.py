@@ -1,4 +1,4 @@
-"""CPU oracle for the 255-bit NTT (forward, inverse, coset).
+"""CPU oracle for the 255-bit NTT (forward, inverse, coset, coset inverse).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference arm of ``bench.py`` may import this package.  The
@@ -27,6 +27,7 @@ from .ntt_oracle import (  # noqa: F401  (re-exported)
     BN254_FR,
     FIELD_BY_INDEX,
     FIELDS,
+    coset_intt,
     coset_ntt,
     dft_direct,
     get_field,
@@ -35,6 +36,7 @@ from .ntt_oracle import (  # noqa: F401  (re-exported)
     intt,
     limbs_to_ints,
     ntt,
+    quotient_pointwise,
     root_of_unity,
     transform,
 )
@@ -45,7 +47,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle_ntt.so")
 _lock = threading.Lock()
 _lib = None
 
-KIND = {"forward": 0, "inverse": 1, "coset": 2}
+KIND = {"forward": 0, "inverse": 1, "coset": 2, "coset_inverse": 3}
 
 
 def build_c_oracle(force: bool = False) -> str:

@@ -219,7 +219,8 @@ static void radix2(const field_t *F, uint64_t (*a)[4], uint64_t n, unsigned log_
 }
 
 /*
- * kind: 0 forward, 1 inverse, 2 coset forward.
+ * kind: 0 forward, 1 inverse, 2 coset forward, 3 coset inverse
+ *       (x_n = s^-n N^-1 sum_k X_k omega^-nk, the inverse of kind 2).
  * shift: coset shift s (4 limbs, canonical) or NULL for the generator.
  * in/out: n = 2^log_n elements of 4 limbs; in == out allowed.
  * Returns 0 on success, 1 bad field, 2 bad size, 3 bad kind, 4 no memory,
@@ -230,12 +231,12 @@ int oracle_ntt(int field, int kind, unsigned log_n, const uint64_t *shift, const
     if (field < 0 || field > 1) return 1;
     const field_t *F = &FIELDS[field];
     if (log_n < 1 || log_n > F->adicity || log_n > 30) return 2;
-    if (kind < 0 || kind > 2) return 3;
+    if (kind < 0 || kind > 3) return 3;
     uint64_t n = (uint64_t)1 << log_n;
     uint64_t (*a)[4] = (uint64_t(*)[4])malloc(n * 32);
     if (!a) return 4;
     uint64_t s_m[4], p[4];
-    if (kind == 2) {
+    if (kind == 2 || kind == 3) {
         uint64_t s[4] = {F->g, 0, 0, 0};
         if (shift) memcpy(s, shift, sizeof s);
         to_mont(F, s_m, s);
@@ -254,7 +255,7 @@ int oracle_ntt(int field, int kind, unsigned log_n, const uint64_t *shift, const
     }
     uint64_t w[4];
     root_mont(F, log_n, w);
-    if (kind == 1) {
+    if (kind == 1 || kind == 3) {
         uint64_t wi[4];
         inv_mont(F, w, wi);
         radix2(F, a, n, log_n, wi);
@@ -262,6 +263,15 @@ int oracle_ntt(int field, int kind, unsigned log_n, const uint64_t *shift, const
         to_mont(F, nm, nn);
         inv_mont(F, nm, ninv);
         for (uint64_t i = 0; i < n; i++) mont_mul(F, a[i], a[i], ninv);
+        if (kind == 3) {
+            /* x_n *= s^-n */
+            uint64_t si[4];
+            inv_mont(F, s_m, si);
+            for (uint64_t i = 0; i < n; i++) {
+                mont_mul(F, a[i], a[i], p);
+                mont_mul(F, p, p, si);
+            }
+        }
     } else {
         radix2(F, a, n, log_n, w);
     }

@@ -14,8 +14,11 @@ with omega_N a primitive N-th root of unity of the prime field F_M.  The paper
 states the forward transform only; the inverse and the coset transform are the
 standard companions that a prover's evaluation/interpolation step uses:
 
-    inverse:  x_n = N^{-1} * sum_k X_k * omega_N^{-k n}
-    coset:    X_k = sum_n x_n * (s * omega_N^k)^n = forward(x_n * s^n)
+    inverse:        x_n = N^{-1} * sum_k X_k * omega_N^{-k n}
+    coset:          X_k = sum_n x_n * (s * omega_N^k)^n = forward(x_n * s^n)
+    coset inverse:  x_n = s^{-n} * inverse(X)_n, so coset_inverse(coset(x)) = x
+                    (interpolation from a coset, the step after a prover's
+                    pointwise work on the coset evaluations)
 
 Readings of points the paper leaves open:
   * omega_N = g^((M-1)/N) with g the field's multiplicative generator (7 for
@@ -190,6 +193,32 @@ def coset_ntt(field, x, shift: int | None = None) -> list[int]:
     return ntt(f, scaled)
 
 
+def coset_intt(field, X, shift: int | None = None) -> list[int]:
+    """Coset inverse x_n = s^{-n} N^{-1} sum_k X_k omega_N^{-kn}."""
+    f = get_field(field)
+    s = default_coset_shift(f) if shift is None else shift % f.modulus
+    s_inv = inverse(f, s)
+    y = intt(f, X)
+    out = []
+    p = 1
+    for v in y:
+        out.append(v * p % f.modulus)
+        p = p * s_inv % f.modulus
+    return out
+
+
+def quotient_pointwise(field, a, b, c, z) -> list[int]:
+    """out_i = (a_i b_i - c_i) z_(i mod len(z)) mod M, element by element.
+
+    The prover step between the coset transforms and the coset inverse (with
+    z the inverse of the vanishing polynomial on the coset points); not part
+    of the paper, whose workload is the transform itself.
+    """
+    m = get_field(field).modulus
+    L = len(z)
+    return [(int(x) * int(y) - int(w)) * int(z[i % L]) % m for i, (x, y, w) in enumerate(zip(a, b, c))]
+
+
 def horner(field, coeffs, z: int) -> int:
     """Evaluate sum_n coeffs[n] z^n mod M by Horner's rule."""
     f = get_field(field)
@@ -200,13 +229,15 @@ def horner(field, coeffs, z: int) -> int:
 
 
 def transform(field, kind: str, x, shift: int | None = None) -> list[int]:
-    """kind in {'forward', 'inverse', 'coset'}."""
+    """kind in {'forward', 'inverse', 'coset', 'coset_inverse'}."""
     if kind == "forward":
         return ntt(field, x)
     if kind == "inverse":
         return intt(field, x)
     if kind == "coset":
         return coset_ntt(field, x, shift)
+    if kind == "coset_inverse":
+        return coset_intt(field, x, shift)
     raise ValueError(kind)
 
 

@@ -21,6 +21,7 @@ from ._native import (  # noqa: F401
     NttError,
     ntt_batch_submit,
     ntt_coset_forward,
+    ntt_coset_inverse,
     ntt_execute,
     ntt_field_mont_mul,
     ntt_forward,
@@ -32,6 +33,7 @@ from ._native import (  # noqa: F401
     ntt_plan_read_table,
     ntt_plan_set_coset_shift,
     ntt_plan_set_path,
+    ntt_pointwise_quotient,
     ntt_status_string,
     ntt_transform_host,
     ntt_version,
@@ -63,6 +65,9 @@ class Plan:
 
     def coset_forward(self, x, out=None, stream=None):
         return self.run("coset", x, out, stream)
+
+    def coset_inverse(self, x, out=None, stream=None):
+        return self.run("coset_inverse", x, out, stream)
 
     def describe(self) -> dict:
         return ntt_plan_describe(self.handle)

@@ -22,7 +22,7 @@ STATUS_NAMES = {
     4: "NTT_ERR_CUDA", 5: "NTT_ERR_TIMEOUT", 6: "NTT_ERR_BUDGET", 7: "NTT_ERR_NO_DEVICE",
 }
 FIELD = {"bls12_381_fr": 0, "bn254_fr": 1}
-KIND = {"forward": 0, "inverse": 1, "coset": 2}
+KIND = {"forward": 0, "inverse": 1, "coset": 2, "coset_inverse": 3}
 PATH = {"auto": 0, "butterfly": 1, "matrix": 2}
 HEADER = os.path.join(_build.ROOT, "include", "ntt_gb300.h")
 
@@ -77,6 +77,7 @@ _SIGS = {
     "ntt_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ntt_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ntt_coset_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ntt_coset_inverse": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ntt_execute": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "ntt_transform_host": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "ntt_transform_host_async": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
@@ -91,6 +92,8 @@ _SIGS = {
     "ntt_batch_debug_stall": (ctypes.c_int, [ctypes.c_int]),
     "ntt_batch_cache_clear": (ctypes.c_int, []),
     "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
+    "ntt_pointwise_quotient": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(_U64), _U32, _VP, _U64,
+                                              _VP]),
     "ntt_field_mont_mul_rep": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _U32, ctypes.c_int, _VP]),
     "ntt_plan_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ntt_plan_read_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U64)]),
@@ -205,6 +208,10 @@ def ntt_coset_forward(plan: int, d_in, d_out, stream=None) -> None:
     _check(load().ntt_coset_forward(plan, _ptr(d_in), _ptr(d_out), _stream(stream)), "ntt_coset_forward")
 
 
+def ntt_coset_inverse(plan: int, d_in, d_out, stream=None) -> None:
+    _check(load().ntt_coset_inverse(plan, _ptr(d_in), _ptr(d_out), _stream(stream)), "ntt_coset_inverse")
+
+
 def ntt_execute(plan: int, kind, d_in, d_out, stream=None) -> None:
     _check(load().ntt_execute(plan, _kind(kind), _ptr(d_in), _ptr(d_out), _stream(stream)), "ntt_execute")
 
@@ -286,6 +293,17 @@ def ntt_plan_poll_error(plan: int) -> int:
 def ntt_field_mont_mul(field, d_a, d_b, d_out, count: int, stream=None) -> None:
     _check(load().ntt_field_mont_mul(_field(field), _ptr(d_a), _ptr(d_b), _ptr(d_out), int(count), _stream(stream)),
            "ntt_field_mont_mul")
+
+
+def ntt_pointwise_quotient(field, d_a, d_b, d_c, z_values, d_out, count: int, stream=None) -> None:
+    """out[i] = (a[i] b[i] - c[i]) z[i mod len(z)]; z_values: Python ints (host)."""
+    z = [int(v) for v in z_values]
+    arr = (_U64 * (4 * max(1, len(z))))()
+    for j, v in enumerate(z):
+        for k in range(4):
+            arr[4 * j + k] = (v >> (64 * k)) & 0xFFFFFFFFFFFFFFFF
+    _check(load().ntt_pointwise_quotient(_field(field), _ptr(d_a), _ptr(d_b), _ptr(d_c), arr, len(z), _ptr(d_out),
+                                         int(count), _stream(stream)), "ntt_pointwise_quotient")
 
 
 def ntt_plan_enable_timing(plan: int, enable: bool = True) -> None:

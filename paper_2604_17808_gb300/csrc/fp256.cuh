@@ -330,6 +330,26 @@ __device__ __forceinline__ uint32_t mont_mul_coop(uint32_t a_j, uint32_t b_j, ui
   return ge ? t - p_j - borrow_in : t;
 }
 
+// y = x * 2^-256 mod M for canonical x (Montgomery reduction alone: half
+// the multiplies of mont_mul).
+template <class F>
+__device__ __forceinline__ void mont_redc(uint32_t y[8], const uint32_t x[8]) {
+  uint32_t t[9];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t[j] = x[j];
+  t[8] = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t m = mont_m<F>(t[0]);
+    row_even_p<F>(t, m);
+    row_odd_p<F>(t, m);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = t[j + 1];
+    t[8] = 0;
+  }
+  reduce_once<F>(y, t);
+}
+
 __device__ __forceinline__ void fe_copy(uint32_t r[8], const uint32_t a[8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) r[j] = a[j];
@@ -337,26 +357,29 @@ __device__ __forceinline__ void fe_copy(uint32_t r[8], const uint32_t a[8]) {
 
 // ------------------------------------------------------------- memory access
 
-// One element = 32 bytes = two 16-byte vectors.
+// One element = 32 bytes, moved with one 256-bit access (ld/st .v8.b32,
+// sm_100 and later); element addresses are 32-byte aligned.
 __device__ __forceinline__ void fe_load_global(uint32_t r[8], const uint4 *base, uint64_t elem) {
-  const uint4 lo = __ldg(base + 2 * elem);
-  const uint4 hi = __ldg(base + 2 * elem + 1);
-  r[0] = lo.x; r[1] = lo.y; r[2] = lo.z; r[3] = lo.w;
-  r[4] = hi.x; r[5] = hi.y; r[6] = hi.z; r[7] = hi.w;
+  asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "l"(base + 2 * elem));
 }
 
 // L2-coherent load (ld.global.cg): for data another CTA wrote earlier in the
-// same kernel launch.
+// same kernel launch (volatile: never moved above the wait that orders it).
 __device__ __forceinline__ void fe_load_global_cg(uint32_t r[8], const uint4 *base, uint64_t elem) {
-  const uint4 lo = __ldcg(base + 2 * elem);
-  const uint4 hi = __ldcg(base + 2 * elem + 1);
-  r[0] = lo.x; r[1] = lo.y; r[2] = lo.z; r[3] = lo.w;
-  r[4] = hi.x; r[5] = hi.y; r[6] = hi.z; r[7] = hi.w;
+  asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(base + 2 * elem)
+               : "memory");
 }
 
 __device__ __forceinline__ void fe_store_global(uint4 *base, uint64_t elem, const uint32_t a[8]) {
-  base[2 * elem] = make_uint4(a[0], a[1], a[2], a[3]);
-  base[2 * elem + 1] = make_uint4(a[4], a[5], a[6], a[7]);
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               :
+               : "l"(base + 2 * elem), "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]),
+                 "r"(a[6]), "r"(a[7])
+               : "memory");
 }
 
 }  // namespace gb300ntt

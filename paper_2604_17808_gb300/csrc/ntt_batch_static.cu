@@ -106,7 +106,7 @@ extern "C" ntt_status ntt_batch_submit_static(const ntt_job *jobs, size_t n, uin
   for (size_t i = 0; i < n; ++i) {
     const ntt_job &j = jobs[i];
     if (!j.plan || j.in == j.out) return NTT_ERR_INVALID_ARG;
-    if (j.kind < 0 || j.kind > 2 || (j.kind == kCoset && !j.plan->has_coset)) return NTT_ERR_INVALID_ARG;
+    if (!kind_is_valid(j.kind, j.plan->has_coset)) return NTT_ERR_INVALID_ARG;
     if (j.plan->path == NTT_PATH_MATRIX) return NTT_ERR_UNSUPPORTED;
     ntt_status s = check_buffer(j.in);
     if (s == NTT_OK) s = check_buffer(j.out);

@@ -38,6 +38,14 @@ struct BatchSeg {
   uint32_t dep_tiles;   // number of tiles of dep_seg
 };
 
+// Multipliers of the pointwise quotient, passed by value (no device table):
+// z_j * 2^512 mod M for j < len, len a power of two <= kMaxQuotientZ.
+constexpr int kMaxQuotientZ = 64;
+struct QuotientZ {
+  Fe32 z[kMaxQuotientZ];
+  uint32_t len;
+};
+
 struct BatchLaunch {
   const BatchSeg *segs;   // device array, sorted by first_item
   uint32_t num_segs;
@@ -67,6 +75,9 @@ struct FieldLaunchers {
                          cudaStream_t st);
   // one matrix-form pass (logs <= 3), `grid` persistent CTAs
   cudaError_t (*matrix_pass)(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st);
+  // out[i] = (a[i] b[i] - c[i]) z[i mod z_len] (z given as z 2^512 mod M)
+  cudaError_t (*quotient)(uint4 *out, const uint4 *a, const uint4 *b, const uint4 *c, const QuotientZ &z,
+                          uint64_t count, cudaStream_t st);
 };
 
 const FieldLaunchers &launchers_bls12_381();

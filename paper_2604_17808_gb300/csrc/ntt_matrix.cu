@@ -158,7 +158,7 @@ ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *
   if (!m || !m->nested) return NTT_ERR_UNSUPPORTED;
   ntt_plan q = m->nested;
   const FieldLaunchers &L = launchers(p->field);
-  const int dir = kind == kInverse ? 1 : 0;
+  const int dir = table_kind(kind) == kInverse ? 1 : 0;
   for (uint32_t j = 0; j < q->num_passes; ++j) {
     MatrixPassArgs ma{};
     int mode = 0;

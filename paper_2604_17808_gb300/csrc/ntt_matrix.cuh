@@ -277,9 +277,11 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
         const uint64_t d = d0 + m;
         if (d < a.num_sub) {
           const uint64_t q = d & mp_mask, o = d >> a.log_mp;
+          const uint64_t pos = q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS));
           uint32_t v[8];
           tile_load(v, reinterpret_cast<const uint4 *>(sA), m * S + k);
-          fe_store_global(a.dst, q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS)), v);
+          if (a.post) post_mul<F>(v, a.post, pos);
+          fe_store_global(a.dst, pos, v);
         }
       } else {
         const uint32_t m = e / S, k = e % S;
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
           const uint64_t rev = reverse_digits(a, d);
           uint32_t v[8];
           tile_load(v, reinterpret_cast<const uint4 *>(sA), m * S + k);
+          if (a.post) post_mul<F>(v, a.post, (rev << LOGS) | k);
           fe_store_global(a.dst, (rev << LOGS) | k, v);
         }
       }

@@ -23,26 +23,28 @@
 // Work split on the GPU: one CTA owns a tile of 2^TL elements in shared
 // memory (TL = 11: 2048 elements, 256 threads; TL = 10: 1024 elements, 128
 // threads) = G = 2^TL / S sub-transforms with consecutive sub-transform
-// index.
-//   load phase : consecutive threads read consecutive 32-byte elements
-//                (coalesced), multiply by the input multiplier (pass >= 1:
-//                omega_M^(n q), read with the same coalesced pattern), and
-//                write the tile;
-//   rounds     : decimation-in-frequency (Gentleman-Sande) radix-2 network
-//                over every sub-transform of the tile, two stages at a time
-//                (radix-4: each thread loads 4 elements, does 4 butterflies,
-//                writes them back), the whole CTA in lockstep with a barrier
-//                between rounds.  The round loop runs at run time so that the
-//                hot code is one radix-4 body (small enough for the
-//                instruction cache).  An odd number of stages starts with a
-//                radix-2 round; the last round (stages 1 and 0) knows its
-//                trivial twiddles at compile time and does 1 multiply per 4
-//                elements instead of 4;
-//   store phase: coalesced 32-byte stores; the DIF output order is undone by
-//                reading the tile at bit-reversed positions.
+// index.  The DIF (Gentleman-Sande) radix-2 network over every
+// sub-transform of the tile runs two stages at a time (radix-4: each thread
+// takes 4 elements, does 4 butterflies, puts them back), the whole CTA in
+// lockstep with a barrier between rounds:
+//   load round : (S >= 16) the top two stages, on elements read straight
+//                from global memory (one 256-bit load each, runs of
+//                consecutive elements across a warp) and multiplied by the
+//                input multiplier (pass >= 1: omega_M^(n q));
+//   rounds     : the stages in between, read from and written back to the
+//                tile; the round loop runs at run time so that the hot code
+//                is one radix-4 body (small enough for the instruction
+//                cache); an odd count starts with a radix-2 round;
+//   store round: the last two stages, whose trivial twiddles are known at
+//                compile time (1 multiply per 4 elements instead of 4),
+//                written straight to global memory at the bit-reversed
+//                output index (this undoes the DIF output order).
+// Sub-transforms of 2..8 points use a staged variant (load phase, rounds,
+// store phase through the tile).
 // The tile is XOR-swizzled on 16-byte chunks (swz); the swizzle was chosen
-// by an exhaustive check so that every access pattern of the three phases,
-// for every sub-transform size 2..2048, is free of bank conflicts.
+// by simulating the shared-memory wavefronts of every access pattern above,
+// for both tile sizes and every sub-transform size 4..2048: none has a bank
+// conflict.
 #pragma once
 
 #include <cstdint>
@@ -90,6 +92,8 @@ struct PassArgs {
   uint4 *dst;            // output elements
   const uint4 *mul;      // input multipliers (Montgomery form) or nullptr
   const uint4 *dft_tw;   // omega_S^i, i < S/2 (Montgomery form)
+  const uint4 *post;     // output multipliers indexed by output position, or nullptr
+                         // (last pass of a coset inverse: s^-n)
   uint64_t num_sub;      // number of sub-transforms in the pass, N / S
   uint32_t log_mp;       // inner: log2 Mp; first: log2(N / S)
   uint32_t num_digits;   // first: P - 1 untransformed digits to reverse
@@ -114,7 +118,7 @@ __device__ __forceinline__ uint64_t reverse_digits(const PassArgs &a, uint64_t d
 // ------------------------------------------------------------- swizzle
 // Chunk c = 2e + h (16-byte half h of tile element e) is stored at
 // c ^ swz(e), swz(e) = XOR of f_b over the set bits b >= 2 of e, with
-// f_2..f_10 = 1,7,3,5,7,1,3,4,1 (3-bit columns).  Packed as three 8-entry
+// f_2..f_10 = 1,7,3,5,7,1,3,5,1 (3-bit columns).  Packed as three 8-entry
 // lookup tables (3 bits per entry) for e bits 2-4, 5-7 and 8-10.
 constexpr uint32_t swz_lut(uint32_t fa, uint32_t fb, uint32_t fc) {
   uint32_t lut = 0;
@@ -126,7 +130,7 @@ constexpr uint32_t swz_lut(uint32_t fa, uint32_t fb, uint32_t fc) {
 }
 constexpr uint32_t kSwzLut0 = swz_lut(1, 7, 3);
 constexpr uint32_t kSwzLut1 = swz_lut(5, 7, 1);
-constexpr uint32_t kSwzLut2 = swz_lut(3, 4, 1);
+constexpr uint32_t kSwzLut2 = swz_lut(3, 5, 1);
 
 __device__ __forceinline__ uint32_t swz(uint32_t e) {
   const uint32_t x0 = (e >> 2) & 7, x1 = (e >> 5) & 7, x2 = (e >> 8) & 7;
@@ -167,16 +171,17 @@ __device__ __forceinline__ void dif_bfly1(uint32_t x[8], uint32_t y[8]) {
   fe_copy(y, d);
 }
 
-// Radix-2 round on bit T = LOGS - 1 (first round when LOGS is odd): pairs
-// (p, p + S/2) with twiddle omega_S^(p mod S/2).
-template <class F, int LOGS, int TL>
-__device__ __forceinline__ void round_radix2_top(uint4 *tile, const uint4 *dft_tw) {
-  constexpr uint32_t H = 1u << (LOGS - 1);
+// Radix-2 round on bit T (compile time): pairs (p, p + 2^T) with twiddle
+// omega_S^((p mod 2^T) * S / 2^(T+1)).  The staged tile runs it first (T =
+// LOGS - 1) when LOGS is odd, the fused tile right after its load round.
+template <class F, int LOGS, int TL, int T>
+__device__ __forceinline__ void round_radix2(uint4 *tile, const uint4 *dft_tw) {
+  constexpr uint32_t H = 1u << T;
 #pragma unroll 1
   for (int i = 0; i < kElemsPerThread / 2; ++i) {
     const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;   // pair index
     const uint32_t low = g & (H - 1);
-    const uint32_t e0 = low | ((g >> (LOGS - 1)) << LOGS);
+    const uint32_t e0 = low | ((g >> T) << (T + 1));
     uint32_t x[8], y[8];
     tile_load(x, tile, e0);
     tile_load(y, tile, e0 | H);
@@ -184,7 +189,7 @@ __device__ __forceinline__ void round_radix2_top(uint4 *tile, const uint4 *dft_t
       dif_bfly1<F>(x, y);
     } else {
       uint32_t w[8];
-      fe_load_global(w, dft_tw, low);
+      fe_load_global(w, dft_tw, low << (LOGS - 1 - T));
       dif_bfly<F>(x, y, w);
     }
     tile_store(tile, e0, x);
@@ -192,16 +197,26 @@ __device__ __forceinline__ void round_radix2_top(uint4 *tile, const uint4 *dft_t
   }
 }
 
-// Radix-4 round on bits [T, T+1], T >= 2 (run-time T).
+// Radix-4 round on bits [T, T+1], T >= 2 (run-time T).  Group g covers
+// positions e0 + {0, 1, 2, 3} * 2^T of one sub-transform; with `dl_fast`
+// (the top round, T = LOGS - 2, on the groups the load phase gave this
+// thread) sub-transforms vary fastest across g, else positions do.
 template <class F, int LOGS, int TL>
-__device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, uint32_t T) {
+__device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, uint32_t T, bool dl_fast = false) {
   const uint32_t step = 1u << T;
   const uint32_t sh = LOGS - 2 - T;
 #pragma unroll 1
   for (int i = 0; i < kGroupsPerThread; ++i) {
     const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;   // group index
-    const uint32_t low = g & (step - 1);
-    const uint32_t e0 = low | ((g >> T) << (T + 2));
+    uint32_t low, e0;
+    if (dl_fast) {
+      constexpr int LOGG = TL - LOGS;
+      low = g >> LOGG;
+      e0 = ((g & ((1u << LOGG) - 1)) << LOGS) | low;
+    } else {
+      low = g & (step - 1);
+      e0 = low | ((g >> T) << (T + 2));
+    }
     uint32_t x0[8], x1[8], x2[8], x3[8], w[8];
     tile_load(x0, tile, e0);
     tile_load(x1, tile, e0 + step);
@@ -247,6 +262,14 @@ __device__ __forceinline__ void round_radix4_last(uint4 *tile, const uint4 *dft_
   }
 }
 
+// x *= post[pos] (Montgomery form multiplier: the result stays standard form).
+template <class F>
+__device__ __forceinline__ void post_mul(uint32_t x[8], const uint4 *post, uint64_t pos) {
+  uint32_t w[8];
+  fe_load_global(w, post, pos);
+  mont_mul<F>(x, x, w);
+}
+
 template <int LOGS>
 __device__ __forceinline__ uint32_t bit_reverse_local(uint32_t p) {
   return __brev(p) >> (32 - LOGS);
@@ -254,12 +277,10 @@ __device__ __forceinline__ uint32_t bit_reverse_local(uint32_t p) {
 
 // ------------------------------------------------------------ pass tile
 
-// Process tile `tile` of one pass.  All threads of the CTA call this.
-// CG = true reads the pass input with ld.global.cg (L2, coherent), for data
-// written earlier in the same kernel launch (the persistent batched kernel);
-// otherwise through the read-only path.
+// Staged tile (sub-transforms of 2..8 points): load phase, rounds, store
+// phase, each separated by a CTA barrier.
 template <class F, int LOGS, int MODE, bool CG, int TL>
-__device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint4 *smem) {
+__device__ __forceinline__ void pass_tile_staged(const PassArgs &a, uint64_t tile, uint4 *smem) {
   static_assert(LOGS <= TL, "sub-transform larger than the tile");
   constexpr uint32_t S = 1u << LOGS;
   constexpr int LOGG = TL - LOGS;
@@ -301,7 +322,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
   // ---------------- DIF rounds, top bit down
   int T = LOGS;
   if constexpr (LOGS & 1) {
-    round_radix2_top<F, LOGS, TL>(smem, a.dft_tw);
+    round_radix2<F, LOGS, TL, LOGS - 1>(smem, a.dft_tw);
     __syncthreads();
     T -= 1;
   }
@@ -327,6 +348,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
         const uint64_t pos = q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS));
         uint32_t v[8];
         tile_load(v, smem, (dl << LOGS) | bit_reverse_local<LOGS>(k));
+        if (a.post) post_mul<F>(v, a.post, pos);
         fe_store_global(a.dst, pos, v);
       }
     } else {
@@ -336,10 +358,230 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
         const uint64_t rev = reverse_digits(a, d);
         uint32_t v[8];
         tile_load(v, smem, (dl << LOGS) | bit_reverse_local<LOGS>(k));
+        if (a.post) post_mul<F>(v, a.post, (rev << LOGS) | k);
         fe_store_global(a.dst, (rev << LOGS) | k, v);
       }
     }
   }
+}
+
+// ------------------------------------------------ fused tile (S >= 16)
+//
+// The first radix-4 round (bits LOGS-1, LOGS-2) takes its four elements
+// straight from global memory and the last one (bits 1, 0) writes its four
+// results straight to global memory.  A warp starts its butterflies as soon
+// as its own loads return and stores as soon as it is done, so in a pass that
+// fits in one wave of CTAs (2^20 points: 1024 tiles on 1064 slots) the memory
+// traffic overlaps the arithmetic of other warps instead of forming a load
+// burst before and a store burst after it; two tile round trips through
+// shared memory and two barriers go away.
+
+// Global position of element n of sub-transform d (pass input; the in-place
+// inner passes write output k of d to the same formula).
+template <int LOGS, int MODE>
+__device__ __forceinline__ uint64_t elem_pos(const PassArgs &a, uint64_t d, uint32_t n) {
+  if constexpr (MODE == kModeInner) {
+    const uint64_t q = d & ((1ull << a.log_mp) - 1), o = d >> a.log_mp;
+    return q + ((uint64_t)n << a.log_mp) + (o << (a.log_mp + LOGS));
+  } else {
+    return d + ((uint64_t)n << a.log_mp);
+  }
+}
+
+// Load round.  Group (dl, low): elements low + j*S/4 (j = 0..3) of
+// sub-transform d0 + dl, sub-transforms varying fastest across threads so
+// that a warp reads runs of consecutive elements.
+template <class F, int LOGS, int MODE, bool CG, int TL>
+__device__ __forceinline__ void round_radix4_load(const PassArgs &a, uint64_t d0, uint4 *tile) {
+  constexpr int LOGG = TL - LOGS;
+  constexpr uint32_t G = 1u << LOGG, Q = 1u << (LOGS - 2);
+#pragma unroll 1
+  for (int i = 0; i < kGroupsPerThread; ++i) {
+    const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;
+    const uint32_t dl = g & (G - 1), low = g >> LOGG;
+    const uint64_t d = d0 + dl;
+    if (d >= a.num_sub) continue;
+    uint32_t x[4][8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t pos = elem_pos<LOGS, MODE>(a, d, low + j * Q);
+      if constexpr (CG) fe_load_global_cg(x[j], a.src, pos);
+      else fe_load_global(x[j], a.src, pos);
+    }
+    if constexpr (MODE != kModeFirst) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t n = low + j * Q;
+        uint32_t w[8];
+        if constexpr (MODE == kModeInner)
+          fe_load_global(w, a.mul, ((uint64_t)n << a.log_mp) + (d & ((1ull << a.log_mp) - 1)));
+        else
+          fe_load_global(w, a.mul, n);
+        mont_mul<F>(x[j], x[j], w);
+      }
+    }
+    uint32_t w[8];
+    // stage on bit LOGS-1: pairs (low, low + S/2), (low + S/4, low + 3S/4)
+    fe_load_global(w, a.dft_tw, low);
+    dif_bfly<F>(x[0], x[2], w);
+    fe_load_global(w, a.dft_tw, low + Q);
+    dif_bfly<F>(x[1], x[3], w);
+    // stage on bit LOGS-2: twiddle omega_S^(2 low) for both pairs
+    fe_load_global(w, a.dft_tw, low << 1);
+    dif_bfly<F>(x[0], x[1], w);
+    dif_bfly<F>(x[2], x[3], w);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tile_store(tile, (dl << LOGS) | (low + j * Q), x[j]);
+  }
+}
+
+// Store round.  Group t of sub-transform dl holds DIF positions
+// p0 = 4 * rev(t) .. p0 + 3 (rev over LOGS-2 bits), whose outputs are
+// k = t, t + S/2, t + S/4, t + 3S/4.  Inner passes vary sub-transforms
+// fastest across threads (consecutive q), pass 0 varies t (consecutive k):
+// either way a warp writes runs of consecutive elements.
+template <class F, int LOGS, int MODE, int TL>
+__device__ __forceinline__ void round_radix4_store(const PassArgs &a, uint64_t d0, const uint4 *tile) {
+  constexpr int LOGG = TL - LOGS;
+  constexpr uint32_t G = 1u << LOGG, Q = 1u << (LOGS - 2);
+  uint32_t w4[8];
+  fe_load_global(w4, a.dft_tw, Q);   // omega_S^(S/4) = omega_4
+#pragma unroll 1
+  for (int i = 0; i < kGroupsPerThread; ++i) {
+    const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;
+    uint32_t dl, t;
+    if constexpr (MODE == kModeInner) {
+      dl = g & (G - 1);
+      t = g >> LOGG;
+    } else {
+      t = g & (Q - 1);
+      dl = g >> (LOGS - 2);
+    }
+    const uint32_t e0 = (dl << LOGS) | (bit_reverse_local<LOGS - 2>(t) << 2);
+    uint32_t x0[8], x1[8], x2[8], x3[8];
+    tile_load(x0, tile, e0);
+    tile_load(x1, tile, e0 + 1);
+    tile_load(x2, tile, e0 + 2);
+    tile_load(x3, tile, e0 + 3);
+    dif_bfly1<F>(x0, x2);
+    dif_bfly<F>(x1, x3, w4);
+    dif_bfly1<F>(x0, x1);
+    dif_bfly1<F>(x2, x3);
+    const uint64_t d = d0 + dl;
+    if (d < a.num_sub) {
+      uint64_t base;
+      uint32_t sh;
+      if constexpr (MODE == kModeInner) {
+        base = elem_pos<LOGS, MODE>(a, d, 0);
+        sh = a.log_mp;
+      } else {
+        base = reverse_digits(a, d) << LOGS;
+        sh = 0;
+      }
+      const uint64_t p0 = base + ((uint64_t)t << sh), p1 = base + ((uint64_t)(t + 2 * Q) << sh);
+      const uint64_t p2 = base + ((uint64_t)(t + Q) << sh), p3 = base + ((uint64_t)(t + 3 * Q) << sh);
+      if (a.post) {   // output multipliers (uniform across the grid)
+        post_mul<F>(x0, a.post, p0);
+        post_mul<F>(x1, a.post, p1);
+        post_mul<F>(x2, a.post, p2);
+        post_mul<F>(x3, a.post, p3);
+      }
+      fe_store_global(a.dst, p0, x0);
+      fe_store_global(a.dst, p1, x1);
+      fe_store_global(a.dst, p2, x2);
+      fe_store_global(a.dst, p3, x3);
+    }
+  }
+}
+
+// Load phase of the compact tile: each thread loads the four elements of
+// each of its two top-round groups (sub-transforms varying fastest across
+// threads: runs of consecutive elements), applies the input multiplier and
+// puts them in the tile, where only this thread reads them next.
+template <class F, int LOGS, int MODE, bool CG, int TL>
+__device__ __forceinline__ void load_own_groups(const PassArgs &a, uint64_t d0, uint4 *tile) {
+  constexpr int LOGG = TL - LOGS;
+  constexpr uint32_t G = 1u << LOGG, Q = 1u << (LOGS - 2);
+#pragma unroll 2
+  for (int k = 0; k < 2 * kGroupsPerThread * 2; ++k) {
+    const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * (k >> 2);
+    const uint32_t dl = g & (G - 1), n = (g >> LOGG) + (k & 3) * Q;
+    const uint64_t d = d0 + dl;
+    if (d < a.num_sub) {
+      uint32_t v[8];
+      const uint64_t pos = elem_pos<LOGS, MODE>(a, d, n);
+      if constexpr (CG) fe_load_global_cg(v, a.src, pos);
+      else fe_load_global(v, a.src, pos);
+      if constexpr (MODE != kModeFirst) {
+        uint32_t w[8];
+        if constexpr (MODE == kModeInner)
+          fe_load_global(w, a.mul, ((uint64_t)n << a.log_mp) + (d & ((1ull << a.log_mp) - 1)));
+        else
+          fe_load_global(w, a.mul, n);
+        mont_mul<F>(v, v, w);
+      }
+      tile_store(tile, (dl << LOGS) | n, v);
+    }
+  }
+}
+
+// Compact tile: as the fused tile, but the load phase and the top round are
+// separate loops over the same per-thread groups (no barrier between them),
+// so the hot code holds one multiply in the load loop and one radix-4 body
+// shared by every round.
+template <class F, int LOGS, int MODE, bool CG, int TL>
+__device__ __forceinline__ void pass_tile_compact(const PassArgs &a, uint64_t tile, uint4 *smem) {
+  static_assert(LOGS >= 4 && LOGS <= TL, "compact tile: 16 <= S <= tile");
+  const uint64_t d0 = tile << (TL - LOGS);
+  load_own_groups<F, LOGS, MODE, CG, TL>(a, d0, smem);
+  round_radix4<F, LOGS, TL>(smem, a.dft_tw, LOGS - 2, true);
+  __syncthreads();
+  constexpr int kMid = LOGS - 4;
+  if constexpr (kMid & 1) {
+    round_radix2<F, LOGS, TL, LOGS - 3>(smem, a.dft_tw);
+    __syncthreads();
+  }
+#pragma unroll 1
+  for (int T = (kMid & 1) ? LOGS - 5 : LOGS - 4; T >= 2; T -= 2) {
+    round_radix4<F, LOGS, TL>(smem, a.dft_tw, (uint32_t)T);
+    __syncthreads();
+  }
+  round_radix4_store<F, LOGS, MODE, TL>(a, d0, smem);
+}
+
+template <class F, int LOGS, int MODE, bool CG, int TL>
+__device__ __forceinline__ void pass_tile_fused(const PassArgs &a, uint64_t tile, uint4 *smem) {
+  static_assert(LOGS >= 4 && LOGS <= TL, "fused tile: 16 <= S <= tile");
+  const uint64_t d0 = tile << (TL - LOGS);
+  round_radix4_load<F, LOGS, MODE, CG, TL>(a, d0, smem);
+  __syncthreads();
+  // stages LOGS-3 .. 2 in between: a radix-2 round first if their count is odd
+  constexpr int kMid = LOGS - 4;
+  if constexpr (kMid & 1) {
+    round_radix2<F, LOGS, TL, LOGS - 3>(smem, a.dft_tw);
+    __syncthreads();
+  }
+#pragma unroll 1
+  for (int T = (kMid & 1) ? LOGS - 5 : LOGS - 4; T >= 2; T -= 2) {
+    round_radix4<F, LOGS, TL>(smem, a.dft_tw, (uint32_t)T);
+    __syncthreads();
+  }
+  round_radix4_store<F, LOGS, MODE, TL>(a, d0, smem);
+}
+
+// Process tile `tile` of one pass.  All threads of the CTA call this; the
+// caller separates two tiles on the same shared memory with a barrier.
+// CG = true reads the pass input with ld.global.cg (L2, coherent), for data
+// written earlier in the same kernel launch (the persistent batched kernel);
+// otherwise through the read-only path.
+#ifndef NTT_PASS_VARIANT
+#define NTT_PASS_VARIANT 0
+#endif
+template <class F, int LOGS, int MODE, bool CG, int TL>
+__device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint4 *smem) {
+  if constexpr (LOGS >= 4 && NTT_PASS_VARIANT == 0) pass_tile_fused<F, LOGS, MODE, CG, TL>(a, tile, smem);
+  else if constexpr (LOGS >= 4 && NTT_PASS_VARIANT == 2) pass_tile_compact<F, LOGS, MODE, CG, TL>(a, tile, smem);
+  else pass_tile_staged<F, LOGS, MODE, CG, TL>(a, tile, smem);
 }
 
 // ------------------------------------------------------------ pass kernel

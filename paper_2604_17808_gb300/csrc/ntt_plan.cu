@@ -156,6 +156,9 @@ ntt_status build_coset_tables(ntt_plan p, const U256 &s, cudaStream_t st) {
       NTT_CUDA(L.gen_2d(p->tw[kCoset][j], logs, log_mp, make_ladder(F, w), p->fac_coset[j], one, st));
     }
   }
+  // coset inverse: x_n *= s^-n on the output of the last pass
+  if (!p->post_coset_inv) NTT_TRY(alloc_tab(p, &p->post_coset_inv, 1ull << log_n));
+  NTT_CUDA(L.gen_1d(p->post_coset_inv, 1ull << log_n, make_ladder(F, F.inv(s)), one, st));
   p->coset_shift = s;
   return NTT_OK;
 }
@@ -219,7 +222,8 @@ ntt_status build_plan(ntt_plan p, cudaStream_t st, const std::vector<uint32_t> *
 // the last pass writes `out`.
 void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j, PassArgs *a, int *mode) {
   const uint32_t P = p->num_passes, log_n = p->log_n;
-  const int dir = kind == kInverse ? 1 : 0;
+  const int tk = table_kind(kind);
+  const int dir = tk == kInverse ? 1 : 0;
   uint4 *work = (P > 1 && in == out) ? p->scratch : (uint4 *)out;
   const uint32_t logs = p->pass_log[j];
   *a = PassArgs{};
@@ -236,7 +240,7 @@ void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j
       a->digit_shift[d - 1] = (uint8_t)shift;
       shift += p->pass_log[d];
     }
-    a->mul = p->pre[kind];
+    a->mul = p->pre[tk];
     *mode = a->mul ? kModeFirstPre : kModeFirst;
   } else {
     uint32_t log_mp = 0;
@@ -244,9 +248,10 @@ void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j
     a->src = work;
     a->dst = j == P - 1 ? (uint4 *)out : work;
     a->log_mp = log_mp;
-    a->mul = p->tw[kind][j];
+    a->mul = p->tw[tk][j];
     *mode = kModeInner;
   }
+  if (kind == kCosetInverse && j == P - 1) a->post = p->post_coset_inv;
 }
 
 // Enqueue one transform: one kernel launch per pass.
@@ -290,7 +295,7 @@ cudaError_t timing_end(ntt_plan p, cudaStream_t st) {
 
 ntt_status check_buffer(const void *ptr) {
   if (!ptr) return NTT_ERR_INVALID_ARG;
-  if ((uintptr_t)ptr % 16) return NTT_ERR_INVALID_ARG;
+  if ((uintptr_t)ptr % 32) return NTT_ERR_INVALID_ARG;   // one element
   return NTT_OK;
 }
 
@@ -389,8 +394,7 @@ ntt_status ntt_plan_destroy(ntt_plan plan) {
 
 ntt_status ntt_execute(ntt_plan plan, ntt_kind kind, const void *d_in, void *d_out, ntt_stream stream) {
   if (!plan) return NTT_ERR_INVALID_ARG;
-  if (kind != NTT_KIND_FORWARD && kind != NTT_KIND_INVERSE && kind != NTT_KIND_COSET) return NTT_ERR_INVALID_ARG;
-  if (kind == NTT_KIND_COSET && !plan->has_coset) return NTT_ERR_INVALID_ARG;
+  if (!kind_is_valid((int)kind, plan->has_coset)) return NTT_ERR_INVALID_ARG;
   NTT_TRY(check_buffer(d_in));
   NTT_TRY(check_buffer(d_out));
   if (plan->path == NTT_PATH_MATRIX) return enqueue_matrix_transform(plan, (int)kind, d_in, d_out, (cudaStream_t)stream);
@@ -402,6 +406,9 @@ ntt_status ntt_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream 
 }
 ntt_status ntt_inverse(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream) {
   return ntt_execute(plan, NTT_KIND_INVERSE, d_in, d_out, stream);
+}
+ntt_status ntt_coset_inverse(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream) {
+  return ntt_execute(plan, NTT_KIND_COSET_INVERSE, d_in, d_out, stream);
 }
 ntt_status ntt_coset_forward(ntt_plan plan, const void *d_in, void *d_out, ntt_stream stream) {
   return ntt_execute(plan, NTT_KIND_COSET, d_in, d_out, stream);
@@ -448,24 +455,28 @@ ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out) {
 ntt_status ntt_plan_read_table(ntt_plan plan, ntt_kind kind, uint32_t pass, uint32_t table, uint64_t first,
                                uint64_t count, void *h_out) {
   if (!plan || !h_out) return NTT_ERR_INVALID_ARG;
-  if (kind != NTT_KIND_FORWARD && kind != NTT_KIND_INVERSE && kind != NTT_KIND_COSET) return NTT_ERR_INVALID_ARG;
+  if (!kind_is_valid((int)kind, true)) return NTT_ERR_INVALID_ARG;
   if (pass >= plan->num_passes) return NTT_ERR_INVALID_ARG;
+  const int tk = table_kind((int)kind);
   const uint32_t logs = plan->pass_log[pass];
   const uint4 *src = nullptr;
   uint64_t size = 0;
   if (table == 0) {
-    src = plan->dft_tw[kind == NTT_KIND_INVERSE ? 1 : 0][logs];
+    src = plan->dft_tw[tk == kInverse ? 1 : 0][logs];
     size = std::max<uint64_t>(1, (1ull << logs) / 2);
   } else if (table == 1) {
     if (pass == 0) {
-      src = plan->pre[kind];
+      src = plan->pre[tk];
       size = 1ull << logs;
     } else {
-      src = plan->tw[kind][pass];
+      src = plan->tw[tk][pass];
       uint32_t log_m = 0;
       for (uint32_t i = 0; i <= pass; ++i) log_m += plan->pass_log[i];
       size = 1ull << log_m;
     }
+  } else if (table == 2) {
+    if (kind == NTT_KIND_COSET_INVERSE && pass == plan->num_passes - 1) src = plan->post_coset_inv;
+    size = 1ull << plan->log_n;
   } else {
     return NTT_ERR_INVALID_ARG;
   }
@@ -532,6 +543,27 @@ ntt_status ntt_field_mont_mul(ntt_field field, const void *d_a, const void *d_b,
   NTT_TRY(check_buffer(d_out));
   return cuda_status(
       launchers((int)field).mul_vec((uint4 *)d_out, (const uint4 *)d_a, (const uint4 *)d_b, count, (cudaStream_t)stream));
+}
+
+ntt_status ntt_pointwise_quotient(ntt_field field, const void *d_a, const void *d_b, const void *d_c,
+                                  const uint64_t *h_z, uint32_t z_len, void *d_out, uint64_t count, ntt_stream stream) {
+  if (field != NTT_FIELD_BLS12_381_FR && field != NTT_FIELD_BN254_FR) return NTT_ERR_INVALID_ARG;
+  if (!h_z || z_len == 0 || z_len > (uint32_t)kMaxQuotientZ || (z_len & (z_len - 1))) return NTT_ERR_INVALID_ARG;
+  NTT_TRY(check_buffer(d_a));
+  NTT_TRY(check_buffer(d_b));
+  NTT_TRY(check_buffer(d_c));
+  NTT_TRY(check_buffer(d_out));
+  const HostField F = host_field((int)field);
+  QuotientZ z{};
+  z.len = z_len;
+  for (uint32_t j = 0; j < z_len; ++j) {
+    const U256 v = from_limbs(h_z + 4 * j);
+    if (u256_geq(v, F.p)) return NTT_ERR_INVALID_ARG;
+    z.z[j] = to_fe32(F.to_mont(F.to_mont(v)));   // z 2^512 mod M
+  }
+  if (count == 0) return NTT_OK;
+  return cuda_status(launchers((int)field).quotient((uint4 *)d_out, (const uint4 *)d_a, (const uint4 *)d_b,
+                                                    (const uint4 *)d_c, z, count, (cudaStream_t)stream));
 }
 
 ntt_status ntt_field_mont_mul_rep(ntt_field field, const void *d_a, const void *d_b, void *d_out, uint64_t count,

@@ -13,7 +13,15 @@
 
 namespace gb300ntt {
 
-enum Kind : int { kForward = 0, kInverse = 1, kCoset = 2 };
+enum Kind : int { kForward = 0, kInverse = 1, kCoset = 2, kCosetInverse = 3 };
+
+// The coset inverse runs the inverse's passes (its tables index kInverse)
+// and multiplies every output x_n by s^-n in the store of the last pass.
+inline int table_kind(int kind) { return kind == kCosetInverse ? kInverse : kind; }
+inline bool kind_is_valid(int kind, bool has_coset) {
+  if (kind < kForward || kind > kCosetInverse) return false;
+  return has_coset || (kind != kCoset && kind != kCosetInverse);
+}
 
 struct MatrixResources;  // tensor-core path (ntt_matrix.cu)
 
@@ -36,6 +44,7 @@ struct ntt_plan_s {
   uint4 *tw[3][gb300ntt::kMaxPasses] = {};  // [kind][pass >= 1]: inter-pass multipliers [S_j][Mp]
   uint4 *pre[3] = {};            // [kind]: pass-0 multipliers [S_0] (coset; single-pass inverse)
   uint4 *fac_coset[gb300ntt::kMaxPasses] = {};  // [pass >= 1]: s^(n N / M_j), n < S_j
+  uint4 *post_coset_inv = nullptr;  // s^-n, n < N: output multipliers of the coset inverse
   uint4 *scratch = nullptr;      // N elements (in-place transforms with > 1 pass)
   uint32_t *d_err = nullptr;     // device error word
   std::vector<void *> allocations;

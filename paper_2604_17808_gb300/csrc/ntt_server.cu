@@ -381,7 +381,7 @@ ntt_status ntt_server_submit(ntt_server s, ntt_field field, ntt_kind kind, uint3
                              void *h_out, uint64_t *ticket) {
   if (!s || !h_in || !h_out || !ticket) return NTT_ERR_INVALID_ARG;
   if (field != NTT_FIELD_BLS12_381_FR && field != NTT_FIELD_BN254_FR) return NTT_ERR_INVALID_ARG;
-  if (kind != NTT_KIND_FORWARD && kind != NTT_KIND_INVERSE && kind != NTT_KIND_COSET) return NTT_ERR_INVALID_ARG;
+  if (!kind_is_valid((int)kind, true)) return NTT_ERR_INVALID_ARG;
   if (log_n < s->cfg.min_log_n || log_n > s->cfg.max_log_n || !s->plans[field][log_n]) return NTT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->error != NTT_OK) return s->error;

@@ -19,7 +19,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = _native.declared_functions()
     for required in ("ntt_plan_create", "ntt_plan_set_path", "ntt_plan_set_coset_shift", "ntt_plan_destroy",
-                     "ntt_forward", "ntt_inverse", "ntt_coset_forward", "ntt_batch_submit", "ntt_status_string"):
+                     "ntt_forward", "ntt_inverse", "ntt_coset_forward", "ntt_coset_inverse", "ntt_batch_submit",
+                     "ntt_status_string"):
         assert required in names
 
 

@@ -89,7 +89,7 @@ def test_batched_mixed_fields_kinds_and_sizes_match_oracle():
     specs = []
     for i, ln in enumerate([1, 2, 5, 9, 11, 12, 13, 16, 17, 20]):
         for field in ("bls12_381_fr", "bn254_fr"):
-            kind = ("forward", "inverse", "coset")[(i + len(field)) % 3]
+            kind = ("forward", "inverse", "coset", "coset_inverse")[(i + len(field)) % 4]
             specs.append((field, ln, kind))
     plans = {}
     jobs, cases = [], []
@@ -123,6 +123,10 @@ def test_batch_rejects_in_place_and_bad_kinds():
         assert e.value.status == 1
         with pytest.raises(N.NttError):
             N.ntt_batch_submit([(plan, "coset", x, y)])  # no coset tables
+        with pytest.raises(N.NttError):
+            N.ntt_batch_submit([(plan, "coset_inverse", x, y)])
+        with pytest.raises(N.NttError):
+            N.ntt_batch_submit([(plan, 4, x, y)])   # unknown kind
         N.ntt_batch_submit([])
     finally:
         N.ntt_plan_destroy(plan)

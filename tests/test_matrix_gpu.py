@@ -25,7 +25,7 @@ from paper_2604_17808_gb300 import _native as N  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 FIELDS = ["bls12_381_fr", "bn254_fr"]
-KINDS = ["forward", "inverse", "coset"]
+KINDS = ["forward", "inverse", "coset", "coset_inverse"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -119,5 +119,8 @@ def test_matrix_path_in_place_and_custom_shift():
         d = dev(x)
         N.ntt_execute(plan, "coset", d, d)
         assert np.array_equal(host(d), oracle.c_transform(field, "coset", x, shift=s))
+        d = dev(x)
+        N.ntt_execute(plan, "coset_inverse", d, d)
+        assert np.array_equal(host(d), oracle.c_transform(field, "coset_inverse", x, shift=s))
     finally:
         N.ntt_plan_destroy(plan)

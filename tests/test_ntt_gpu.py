@@ -3,7 +3,7 @@
 Bar: bit-exact.  All arithmetic is exact modular arithmetic with canonical
 outputs, so the result is unique and the tolerance is zero.
 
-Sizes: every log_n from 1 to 18 for both fields and all three kinds (one,
+Sizes: every log_n from 1 to 18 for both fields and all four kinds (one,
 two and three passes, ragged pass splits, tiles that are only partly
 filled), the full sizes of the workloads (2^12, 2^20 BLS12-381 forward and
 inverse, 2^24 BN254 coset, 2^24 BLS12-381 forward) against stored oracle
@@ -34,7 +34,7 @@ from paper_2604_17808_gb300 import _native as N  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 FIELDS = ["bls12_381_fr", "bn254_fr"]
-KINDS = ["forward", "inverse", "coset"]
+KINDS = ["forward", "inverse", "coset", "coset_inverse"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -63,7 +63,7 @@ def golden():
 def gpu_transform(field, kind, x, log_n=None, plan=None, inplace=False):
     own = plan is None
     if own:
-        plan = N.ntt_plan_create(field, log_n, coset=(kind == "coset"))
+        plan = N.ntt_plan_create(field, log_n, coset=kind in ("coset", "coset_inverse"))
     try:
         d_in = dev(x)
         d_out = d_in if inplace else torch.empty_like(d_in)
@@ -172,9 +172,11 @@ def test_custom_coset_shift(field):
     try:
         N.ntt_plan_set_coset_shift(plan, s)
         got = gpu_transform(field, "coset", x, plan=plan)
+        back = gpu_transform(field, "coset_inverse", x, plan=plan)
     finally:
         N.ntt_plan_destroy(plan)
     assert np.array_equal(got, oracle.c_transform(field, "coset", x, shift=s))
+    assert np.array_equal(back, oracle.c_transform(field, "coset_inverse", x, shift=s))
 
 
 # ------------------------------------------------------------ tables
@@ -216,6 +218,14 @@ def test_device_twiddle_tables_match_oracle_roots(field):
         s = O.default_coset_shift(f)
         step = pow(s, (1 << log_n) // S0, p)
         assert O.limbs_to_ints(buf) == [pow(step, i, p) for i in range(S0)]
+        # coset inverse output multipliers of the last pass: s^-n
+        count = 1 << log_n
+        buf = np.zeros((count, 4), dtype=np.uint64)
+        N.ntt_plan_read_table(plan, "coset_inverse", len(logs) - 1, 2, 0, count, buf)
+        got = O.limbs_to_ints(buf)
+        s_inv = pow(s, p - 2, p)
+        for n in list(range(0, count, 4099)) + [1, count - 1]:
+            assert got[n] == pow(s_inv, n, p)
     finally:
         N.ntt_plan_destroy(plan)
 
@@ -271,8 +281,14 @@ def test_bn254_2_24_coset_matches_digest_and_sampled_outputs():
     x = uniform_elements(field, 1 << log_n, config_seed(3))
     g = _golden_case(3, "coset")
     assert digest(x) == g["input_sha256"]
-    got = gpu_transform(field, "coset", x, log_n)
+    plan = N.ntt_plan_create(field, log_n, coset=True)
+    try:
+        got = gpu_transform(field, "coset", x, plan=plan)
+        back = gpu_transform(field, "coset_inverse", got, plan=plan)
+    finally:
+        N.ntt_plan_destroy(plan)
     assert digest(got) == g["output_sha256"]
+    assert np.array_equal(back, x)   # the coset inverse undoes the coset transform
     _horner_spot_checks(field, x, got, "coset", samples=2, seed=3)
 
 
@@ -349,9 +365,14 @@ def test_argument_errors_are_reported():
         with pytest.raises(N.NttError) as e:
             N.ntt_coset_forward(plan, buf, buf)  # plan built without coset tables
         assert e.value.status == 1
+        with pytest.raises(N.NttError):
+            N.ntt_coset_inverse(plan, buf, buf)
         lib = N.load()
         assert lib.ntt_forward(plan, None, buf.data_ptr(), None) == 1
         assert lib.ntt_forward(plan, buf.data_ptr() + 8, buf.data_ptr(), None) == 1  # misaligned
+        # 16-byte but not 32-byte aligned: every element moves as one 256-bit
+        # access, so buffers must be 32-byte aligned
+        assert lib.ntt_forward(plan, buf.data_ptr() + 16, buf.data_ptr(), None) == 1
         assert lib.ntt_execute(plan, 9, buf.data_ptr(), buf.data_ptr(), None) == 1
         assert lib.ntt_plan_set_coset_shift(plan, None) == 1
         assert N.ntt_plan_poll_error(plan) == 0

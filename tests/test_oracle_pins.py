@@ -10,6 +10,12 @@ Each pin is a fact the mathematics or an independent library fixes:
   * closed forms for special vectors (delta_0, ones, delta_1);
   * the convolution theorem against a schoolbook polynomial product;
   * coset outputs against Horner evaluation at s * omega^k;
+  * the coset inverse against the evaluations of monomials z^m on the coset
+    (it must return the unit vector e_m) and the literal definition;
+  * the pointwise quotient through a whole prover step: with
+    C = A B - (X^n - 1) Q built by schoolbook polynomial arithmetic, coset
+    transforms, the quotient by the vanishing polynomial and the coset
+    inverse must give back Q exactly;
   * the inverse round trip and linearity;
   * the Python oracle against the independent C oracle.
 The mutation tests at the end plant plausible mistakes in a copy of the
@@ -168,8 +174,65 @@ def pin_roundtrip_linearity(impl, field, n=256):
     return lhs == [(u + c * v) % r for u, v in zip(X, Y)]
 
 
+def pin_coset_inverse(impl, field, n=64):
+    # interpolation from the coset {s omega^k}: the evaluations of z^m there
+    # are the coefficient vector e_m; small sizes against the literal
+    # definition x_n = s^-n N^-1 sum_k X_k omega^-nk; and it undoes coset_ntt
+    r = field.modulus
+    s = field.generator
+    w = pow(field.generator, (r - 1) // n, r)
+    for m in (0, 1, 5, n - 1):
+        X = [pow(s * pow(w, k, r) % r, m, r) for k in range(n)]
+        if impl.coset_intt(field, X, s) != [1 if j == m else 0 for j in range(n)]:
+            return False
+    for nn in (2, 4, 16):
+        ww = pow(field.generator, (r - 1) // nn, r)
+        X = rand_vec(field, nn, 5500 + nn)
+        ninv = pow(nn, r - 2, r)
+        sinv = pow(s, r - 2, r)
+        # omega^-jk = omega^((nn - jk mod nn) mod nn)
+        want = [pow(sinv, j, r) * ninv * sum(X[k] * pow(ww, (nn - j * k % nn) % nn, r) for k in range(nn)) % r
+                for j in range(nn)]
+        if impl.coset_intt(field, X, s) != want:
+            return False
+    x = rand_vec(field, n, 5600)
+    return impl.coset_intt(field, impl.coset_ntt(field, x, s), s) == x
+
+
+def _poly_mul(a, b, r):
+    out = [0] * (len(a) + len(b) - 1)
+    for i, u in enumerate(a):
+        for j, v in enumerate(b):
+            out[i + j] = (out[i + j] + u * v) % r
+    return out
+
+
+def pin_quotient_pipeline(impl, field, n=16, blowup=4):
+    # A, B, Q of degree < n; C = A B - (X^n - 1) Q, so (A B - C) / (X^n - 1)
+    # = Q exactly.  On the coset s<omega_m> (m = blowup n) the vanishing
+    # polynomial X^n - 1 takes the values s^n omega_blowup^j - 1, j = k mod blowup.
+    r = field.modulus
+    m = blowup * n
+    s = field.generator
+    A = rand_vec(field, n, 5700)
+    B = rand_vec(field, n, 5701)
+    Q = rand_vec(field, n, 5702)
+    AB = _poly_mul(A, B, r)                         # degree 2n - 2
+    ZQ = [0] * n + Q                                # X^n Q
+    C = [(AB[i] if i < len(AB) else 0) - (ZQ[i] if i < len(ZQ) else 0) + (Q[i] if i < n else 0)
+         for i in range(2 * n)]
+    C = [v % r for v in C]
+    pad = lambda v: list(v) + [0] * (m - len(v))    # noqa: E731
+    a, b, c = (impl.coset_ntt(field, pad(v), s) for v in (A, B, C))
+    w_b = pow(field.generator, (r - 1) // blowup, r)
+    sn = pow(s, n, r)
+    z = [pow((sn * pow(w_b, j, r) - 1) % r, r - 2, r) for j in range(blowup)]
+    t = impl.quotient_pointwise(field, a, b, c, z)
+    return impl.coset_intt(field, t, s) == pad(Q)
+
+
 ALL_PINS = [pin_sympy, pin_brute_force, pin_special_vectors, pin_convolution,
-            pin_coset_horner, pin_roundtrip_linearity]
+            pin_coset_horner, pin_roundtrip_linearity, pin_coset_inverse, pin_quotient_pipeline]
 
 
 @pytest.mark.parametrize("field", FIELDS, ids=FIELD_IDS)
@@ -189,7 +252,7 @@ def test_direct_definition_equals_radix2(field):
 
 
 @pytest.mark.parametrize("field", FIELDS, ids=FIELD_IDS)
-@pytest.mark.parametrize("kind", ["forward", "inverse", "coset"])
+@pytest.mark.parametrize("kind", ["forward", "inverse", "coset", "coset_inverse"])
 def test_c_oracle_matches_python_oracle(field, kind):
     for log_n in list(range(1, 11)) + [12]:
         n = 1 << log_n
@@ -258,7 +321,8 @@ def test_c_oracle_rejects_bad_arguments():
 
 
 def _mutant(**overrides):
-    ns = types.SimpleNamespace(ntt=O.ntt, intt=O.intt, coset_ntt=O.coset_ntt, dft_direct=O.dft_direct)
+    ns = types.SimpleNamespace(ntt=O.ntt, intt=O.intt, coset_ntt=O.coset_ntt, coset_intt=O.coset_intt,
+                               quotient_pointwise=O.quotient_pointwise, dft_direct=O.dft_direct)
     for k, v in overrides.items():
         setattr(ns, k, v)
     return ns
@@ -315,6 +379,28 @@ def _coset_off_by_one(field, x, s=None):  # x_n s^(n+1)
     return O.ntt(field, [v * pow(s, i + 1, r) % r for i, v in enumerate(x)])
 
 
+def _coset_inverse_wrong_sign(field, X, s=None):  # x_n s^(+n) instead of s^(-n)
+    s = field.generator if s is None else s
+    r = field.modulus
+    return [v * pow(s, i, r) % r for i, v in enumerate(O.intt(field, X))]
+
+
+def _coset_inverse_unscaled(field, X, s=None):  # N^-1 dropped
+    n = len(X)
+    r = field.modulus
+    return [v * n % r for v in O.coset_intt(field, X, s)]
+
+
+def _quotient_shifted_z(field, a, b, c, z):  # z index off by one
+    r = field.modulus
+    return [(x * y - w) * z[(i + 1) % len(z)] % r for i, (x, y, w) in enumerate(zip(a, b, c))]
+
+
+def _quotient_sign(field, a, b, c, z):        # (a b + c) instead of (a b - c)
+    r = field.modulus
+    return [(x * y + w) * z[i % len(z)] % r for i, (x, y, w) in enumerate(zip(a, b, c))]
+
+
 def _ntt_transposed_output(field, x):   # output index bit-reversed (a transposed four-step)
     X = O.ntt(field, x)
     return O._bit_reverse_permute(X)
@@ -328,6 +414,10 @@ MUTANTS = {
     "inverse_wrong_root": _mutant(intt=_intt_conjugate_missing),
     "coset_off_by_one": _mutant(coset_ntt=_coset_off_by_one),
     "output_bit_reversed": _mutant(ntt=_ntt_transposed_output),
+    "coset_inverse_wrong_sign": _mutant(coset_intt=_coset_inverse_wrong_sign),
+    "coset_inverse_unscaled": _mutant(coset_intt=_coset_inverse_unscaled),
+    "quotient_shifted_z": _mutant(quotient_pointwise=_quotient_shifted_z),
+    "quotient_sign": _mutant(quotient_pointwise=_quotient_sign),
 }
 
 

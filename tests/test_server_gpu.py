@@ -22,7 +22,7 @@ if not torch.cuda.is_available():
 from paper_2604_17808_gb300 import _native as N  # noqa: E402
 
 FIELDS = ["bls12_381_fr", "bn254_fr"]
-KINDS = ["forward", "inverse", "coset"]
+KINDS = ["forward", "inverse", "coset", "coset_inverse"]
 
 
 @pytest.fixture(scope="module", autouse=True)
