@@ -243,12 +243,12 @@ ntt_status ntt_batch_submit(const ntt_job *jobs, size_t n, ntt_stream stream);
 /*
  * ntt_batch_submit without any allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
- * while they submit work -- code that runs while a stream is being captured
- * into a CUDA graph (cudaMalloc is not a capturable operation and
- * synchronises the device), and services that reserve all their device
- * memory up front and must not allocate once they are serving.
- * ntt_batch_submit allocates a work-item table and counters per new job list
- * and captures a CUDA graph; this call instead runs the same persistent
+ * while they submit work -- services that reserve all their device memory
+ * up front and must not allocate once they are serving, and submitters on
+ * a latency path, where cudaMalloc's implicit device synchronisation would
+ * stall work already queued on other streams.
+ * ntt_batch_submit allocates a work-item table and counters per new job
+ * list; this call instead runs the same persistent
  * batched kernel with its table and counters in one fixed-size array that
  * the library holds in device memory (about 55 KB on every GPU that loads
  * the library, until the process exits).  It calls no cudaMalloc, cudaFree
@@ -262,8 +262,8 @@ ntt_status ntt_batch_submit(const ntt_job *jobs, size_t n, ntt_stream stream);
  * ran out; may be NULL.
  *
  * The first call on a device looks up the array's device address once
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call on a device shares the one array, which keeps the
+ * (cudaGetSymbolAddress).  Every call on a device shares the one array,
+ * which keeps the
  * last call's contents (the call clears the counters it needs): calls whose
  * work overlaps on the GPU race -- order them on one stream.
  */

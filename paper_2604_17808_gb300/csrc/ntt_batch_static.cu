@@ -1,15 +1,15 @@
 // ntt_batch_static.cu -- batched submission that allocates nothing.
 //
 // ntt_batch_submit allocates a work-item table and counters for every new
-// job list (cudaMalloc) and captures a CUDA graph.  Some callers cannot do
-// that on their submission path: code running while a stream is being
-// captured into a CUDA graph (cudaMalloc is not a capturable operation and
-// synchronises the device), and services that reserve all device memory up
-// front and must not allocate once they serve requests.  For them,
+// job list (cudaMalloc).  Some callers cannot allocate on their submission
+// path: services that reserve all device memory up front and must not
+// allocate once they serve requests, and submitters on a latency path,
+// where cudaMalloc's implicit device synchronisation would stall work
+// already queued on other streams.  For them,
 // ntt_batch_submit_static runs the same persistent batched kernel with its
 // work-item table and counters in one file-scope device array of fixed size,
 // instead of allocated memory.  Its host side uses only fixed-size stack
-// arrays: no cudaMalloc, cudaFree, graph capture or heap allocation.
+// arrays: no cudaMalloc, cudaFree or heap allocation.
 #include <cuda_runtime.h>
 
 #include <algorithm>

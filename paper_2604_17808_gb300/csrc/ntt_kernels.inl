@@ -103,9 +103,9 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
 template <int LOGS>
 __device__ __forceinline__ void batch_tile_logs(const BatchSeg &sg, uint64_t tile, uint4 *smem) {
   switch (sg.mode) {
-    case kModeInner: pass_tile<F, LOGS, kModeInner, true, 11>(sg.a, tile, smem); break;
-    case kModeFirst: pass_tile<F, LOGS, kModeFirst, true, 11>(sg.a, tile, smem); break;
-    default: pass_tile<F, LOGS, kModeFirstPre, true, 11>(sg.a, tile, smem); break;
+    case kModeInner: pass_tile<F, LOGS, kModeInner, true, 11, true>(sg.a, tile, smem); break;
+    case kModeFirst: pass_tile<F, LOGS, kModeFirst, true, 11, true>(sg.a, tile, smem); break;
+    default: pass_tile<F, LOGS, kModeFirstPre, true, 11, true>(sg.a, tile, smem); break;
   }
 }
 
@@ -214,10 +214,23 @@ __global__ void mul_rep_coop_kernel(uint32_t *out, const uint32_t *a, const uint
   if (live) out[elem * 8 + j] = x;
 }
 
+// The fused tile is instantiated for the 1024-element tile only: that is
+// the shape of the one-wave passes it is chosen for (sizes up to 2^20).
+template <int LOGS, int TL>
+constexpr bool has_fused() {
+  return TL == 10 && LOGS >= 4;
+}
+
 template <int LOGS, int MODE, int TL>
 cudaError_t set_pass_attr() {
-  return cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TileCfg<TL>::kBytes);
+  cudaError_t e = cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<TL>::kBytes);
+  if constexpr (has_fused<LOGS, TL>()) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TileCfg<TL>::kBytes);
+  }
+  return e;
 }
 
 template <int LOGS, int TL>
@@ -293,42 +306,50 @@ cudaError_t prepare() {
   return e;
 }
 
-template <int LOGS, int TL>
-cudaError_t pass_logs(int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+template <int LOGS, int TL, bool FUSED>
+cudaError_t pass_launch(int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
   const dim3 grid((unsigned)tiles), block(TileCfg<TL>::kThreads);
   const int smem = TileCfg<TL>::kBytes;
   switch (mode) {
-    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner, TL><<<grid, block, smem, st>>>(a); break;
-    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst, TL><<<grid, block, smem, st>>>(a); break;
-    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre, TL><<<grid, block, smem, st>>>(a); break;
+    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner, TL, FUSED><<<grid, block, smem, st>>>(a); break;
+    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst, TL, FUSED><<<grid, block, smem, st>>>(a); break;
+    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre, TL, FUSED><<<grid, block, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
+template <int LOGS, int TL>
+cudaError_t pass_logs(int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  if constexpr (has_fused<LOGS, TL>()) {
+    if (fused) return pass_launch<LOGS, TL, true>(mode, a, tiles, st);
+  }
+  return pass_launch<LOGS, TL, false>(mode, a, tiles, st);
+}
+
 template <int TL>
-cudaError_t pass_tl(int logs, int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+cudaError_t pass_tl(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
   switch (logs) {
-    case 1: return pass_logs<1, TL>(mode, a, tiles, st);
-    case 2: return pass_logs<2, TL>(mode, a, tiles, st);
-    case 3: return pass_logs<3, TL>(mode, a, tiles, st);
-    case 4: return pass_logs<4, TL>(mode, a, tiles, st);
-    case 5: return pass_logs<5, TL>(mode, a, tiles, st);
-    case 6: return pass_logs<6, TL>(mode, a, tiles, st);
-    case 7: return pass_logs<7, TL>(mode, a, tiles, st);
-    case 8: return pass_logs<8, TL>(mode, a, tiles, st);
-    case 9: return pass_logs<9, TL>(mode, a, tiles, st);
-    case 10: return pass_logs<10, TL>(mode, a, tiles, st);
+    case 1: return pass_logs<1, TL>(mode, fused, a, tiles, st);
+    case 2: return pass_logs<2, TL>(mode, fused, a, tiles, st);
+    case 3: return pass_logs<3, TL>(mode, fused, a, tiles, st);
+    case 4: return pass_logs<4, TL>(mode, fused, a, tiles, st);
+    case 5: return pass_logs<5, TL>(mode, fused, a, tiles, st);
+    case 6: return pass_logs<6, TL>(mode, fused, a, tiles, st);
+    case 7: return pass_logs<7, TL>(mode, fused, a, tiles, st);
+    case 8: return pass_logs<8, TL>(mode, fused, a, tiles, st);
+    case 9: return pass_logs<9, TL>(mode, fused, a, tiles, st);
+    case 10: return pass_logs<10, TL>(mode, fused, a, tiles, st);
     case 11:
-      if constexpr (TL >= 11) return pass_logs<11, TL>(mode, a, tiles, st);
+      if constexpr (TL >= 11) return pass_logs<11, TL>(mode, fused, a, tiles, st);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t pass(int logs, int mode, int tl, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
-  if (tl == 11) return pass_tl<11>(logs, mode, a, tiles, st);
-  if (tl == 10) return pass_tl<10>(logs, mode, a, tiles, st);
+cudaError_t pass(int logs, int mode, int tl, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  if (tl == 11) return pass_tl<11>(logs, mode, fused, a, tiles, st);
+  if (tl == 10) return pass_tl<10>(logs, mode, fused, a, tiles, st);
   return cudaErrorInvalidValue;
 }
 

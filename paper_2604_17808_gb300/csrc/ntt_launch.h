@@ -59,8 +59,9 @@ struct BatchLaunch {
 
 struct FieldLaunchers {
   cudaError_t (*prepare)();
-  // one pass; tl = log2 of the tile (10 or 11), logs <= tl
-  cudaError_t (*pass)(int logs, int mode, int tl, const PassArgs &a, uint64_t tiles, cudaStream_t st);
+  // one pass; tl = log2 of the tile (10 or 11), logs <= tl; fused selects the
+  // fused tile where one exists (tl = 10, logs >= 4), else the staged one
+  cudaError_t (*pass)(int logs, int mode, int tl, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st);
   // out[n * Mp + q] = init * fac[n] * base^(n*q)    (fac may be null)
   cudaError_t (*gen_2d)(uint4 *out, uint32_t log_s, uint32_t log_mp, const Pow2Table &pw, const uint4 *fac,
                         Fe32 init, cudaStream_t st);

@@ -197,26 +197,16 @@ __device__ __forceinline__ void round_radix2(uint4 *tile, const uint4 *dft_tw) {
   }
 }
 
-// Radix-4 round on bits [T, T+1], T >= 2 (run-time T).  Group g covers
-// positions e0 + {0, 1, 2, 3} * 2^T of one sub-transform; with `dl_fast`
-// (the top round, T = LOGS - 2, on the groups the load phase gave this
-// thread) sub-transforms vary fastest across g, else positions do.
+// Radix-4 round on bits [T, T+1], T >= 2 (run-time T).
 template <class F, int LOGS, int TL>
-__device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, uint32_t T, bool dl_fast = false) {
+__device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, uint32_t T) {
   const uint32_t step = 1u << T;
   const uint32_t sh = LOGS - 2 - T;
 #pragma unroll 1
   for (int i = 0; i < kGroupsPerThread; ++i) {
     const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;   // group index
-    uint32_t low, e0;
-    if (dl_fast) {
-      constexpr int LOGG = TL - LOGS;
-      low = g >> LOGG;
-      e0 = ((g & ((1u << LOGG) - 1)) << LOGS) | low;
-    } else {
-      low = g & (step - 1);
-      e0 = low | ((g >> T) << (T + 2));
-    }
+    const uint32_t low = g & (step - 1);
+    const uint32_t e0 = low | ((g >> T) << (T + 2));
     uint32_t x0[8], x1[8], x2[8], x3[8], w[8];
     tile_load(x0, tile, e0);
     tile_load(x1, tile, e0 + step);
@@ -494,61 +484,6 @@ __device__ __forceinline__ void round_radix4_store(const PassArgs &a, uint64_t d
   }
 }
 
-// Load phase of the compact tile: each thread loads the four elements of
-// each of its two top-round groups (sub-transforms varying fastest across
-// threads: runs of consecutive elements), applies the input multiplier and
-// puts them in the tile, where only this thread reads them next.
-template <class F, int LOGS, int MODE, bool CG, int TL>
-__device__ __forceinline__ void load_own_groups(const PassArgs &a, uint64_t d0, uint4 *tile) {
-  constexpr int LOGG = TL - LOGS;
-  constexpr uint32_t G = 1u << LOGG, Q = 1u << (LOGS - 2);
-#pragma unroll 2
-  for (int k = 0; k < 2 * kGroupsPerThread * 2; ++k) {
-    const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * (k >> 2);
-    const uint32_t dl = g & (G - 1), n = (g >> LOGG) + (k & 3) * Q;
-    const uint64_t d = d0 + dl;
-    if (d < a.num_sub) {
-      uint32_t v[8];
-      const uint64_t pos = elem_pos<LOGS, MODE>(a, d, n);
-      if constexpr (CG) fe_load_global_cg(v, a.src, pos);
-      else fe_load_global(v, a.src, pos);
-      if constexpr (MODE != kModeFirst) {
-        uint32_t w[8];
-        if constexpr (MODE == kModeInner)
-          fe_load_global(w, a.mul, ((uint64_t)n << a.log_mp) + (d & ((1ull << a.log_mp) - 1)));
-        else
-          fe_load_global(w, a.mul, n);
-        mont_mul<F>(v, v, w);
-      }
-      tile_store(tile, (dl << LOGS) | n, v);
-    }
-  }
-}
-
-// Compact tile: as the fused tile, but the load phase and the top round are
-// separate loops over the same per-thread groups (no barrier between them),
-// so the hot code holds one multiply in the load loop and one radix-4 body
-// shared by every round.
-template <class F, int LOGS, int MODE, bool CG, int TL>
-__device__ __forceinline__ void pass_tile_compact(const PassArgs &a, uint64_t tile, uint4 *smem) {
-  static_assert(LOGS >= 4 && LOGS <= TL, "compact tile: 16 <= S <= tile");
-  const uint64_t d0 = tile << (TL - LOGS);
-  load_own_groups<F, LOGS, MODE, CG, TL>(a, d0, smem);
-  round_radix4<F, LOGS, TL>(smem, a.dft_tw, LOGS - 2, true);
-  __syncthreads();
-  constexpr int kMid = LOGS - 4;
-  if constexpr (kMid & 1) {
-    round_radix2<F, LOGS, TL, LOGS - 3>(smem, a.dft_tw);
-    __syncthreads();
-  }
-#pragma unroll 1
-  for (int T = (kMid & 1) ? LOGS - 5 : LOGS - 4; T >= 2; T -= 2) {
-    round_radix4<F, LOGS, TL>(smem, a.dft_tw, (uint32_t)T);
-    __syncthreads();
-  }
-  round_radix4_store<F, LOGS, MODE, TL>(a, d0, smem);
-}
-
 template <class F, int LOGS, int MODE, bool CG, int TL>
 __device__ __forceinline__ void pass_tile_fused(const PassArgs &a, uint64_t tile, uint4 *smem) {
   static_assert(LOGS >= 4 && LOGS <= TL, "fused tile: 16 <= S <= tile");
@@ -574,23 +509,27 @@ __device__ __forceinline__ void pass_tile_fused(const PassArgs &a, uint64_t tile
 // CG = true reads the pass input with ld.global.cg (L2, coherent), for data
 // written earlier in the same kernel launch (the persistent batched kernel);
 // otherwise through the read-only path.
-#ifndef NTT_PASS_VARIANT
-#define NTT_PASS_VARIANT 0
-#endif
-template <class F, int LOGS, int MODE, bool CG, int TL>
+//
+// FUSED selects the fused tile (sub-transforms of 16 points and more) or the
+// staged one.  Measured on GB300: the fused tile wins where a pass is one
+// wave of CTAs (all CTAs in the same phase: 2^20 pass 0 -6%) and in the
+// persistent batched kernel; the staged tile wins in many-wave passes
+// (2^24: inner passes 1.42 vs 1.61 ms), where CTAs in different phases
+// share the SM and the fused tile's larger hot code misses the
+// instruction cache (no_instruction becomes the top stall).
+template <class F, int LOGS, int MODE, bool CG, int TL, bool FUSED>
 __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint4 *smem) {
-  if constexpr (LOGS >= 4 && NTT_PASS_VARIANT == 0) pass_tile_fused<F, LOGS, MODE, CG, TL>(a, tile, smem);
-  else if constexpr (LOGS >= 4 && NTT_PASS_VARIANT == 2) pass_tile_compact<F, LOGS, MODE, CG, TL>(a, tile, smem);
+  if constexpr (FUSED && LOGS >= 4) pass_tile_fused<F, LOGS, MODE, CG, TL>(a, tile, smem);
   else pass_tile_staged<F, LOGS, MODE, CG, TL>(a, tile, smem);
 }
 
 // ------------------------------------------------------------ pass kernel
 
-template <class F, int LOGS, int MODE, int TL>
+template <class F, int LOGS, int MODE, int TL, bool FUSED>
 __global__ void __launch_bounds__(TileCfg<TL>::kThreads, TileCfg<TL>::kMinBlocks)
     ntt_pass_kernel(const PassArgs a) {
   extern __shared__ uint4 smem[];
-  pass_tile<F, LOGS, MODE, false, TL>(a, blockIdx.x, smem);
+  pass_tile<F, LOGS, MODE, false, TL, FUSED>(a, blockIdx.x, smem);
 }
 
 }  // namespace gb300ntt

@@ -124,6 +124,21 @@ static ntt_status alloc_tab(ntt_plan p, uint4 **out, uint64_t elems) {
   return NTT_OK;
 }
 
+// Free every device table of plan p and clear every pointer to one (the
+// plan keeps its device, field, size and error word), so that build_plan
+// can run again.  Every table allocated by alloc_tab must be listed here.
+void release_plan_tables(ntt_plan p) {
+  for (void *ptr : p->allocations) cudaFree(ptr);
+  p->allocations.clear();
+  p->device_bytes = 0;
+  std::memset(p->dft_tw, 0, sizeof p->dft_tw);
+  std::memset(p->tw, 0, sizeof p->tw);
+  std::memset(p->pre, 0, sizeof p->pre);
+  std::memset(p->fac_coset, 0, sizeof p->fac_coset);
+  p->post_coset_inv = nullptr;
+  p->scratch = nullptr;
+}
+
 #define NTT_TRY(expr)                  \
   do {                                 \
     ntt_status _s = (expr);            \
@@ -254,6 +269,14 @@ void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j
   if (kind == kCosetInverse && j == P - 1) a->post = p->post_coset_inv;
 }
 
+// Tile structure of a pass: the fused tile when the pass is one wave of
+// 1024-element tiles (every CTA resident at once, 7 per SM), the staged
+// tile otherwise (see pass_tile in ntt_pass.cuh for the measurements).
+bool use_fused_tile(ntt_plan p, uint32_t logs, uint32_t tl) {
+  return tl == 10 && logs >= 4 &&
+         pass_tiles(p->log_n, logs, tl) <= (uint64_t)p->sm_count * (uint64_t)TileCfg<10>::kMinBlocks;
+}
+
 // Enqueue one transform: one kernel launch per pass.
 ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st) {
   const FieldLaunchers &L = launchers(p->field);
@@ -264,7 +287,8 @@ ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cu
     const uint32_t logs = p->pass_log[j];
     cudaError_t e = timing_begin(p, (int)j, st);
     const uint32_t tl = p->pass_tl[j];
-    if (e == cudaSuccess) e = L.pass((int)logs, mode, (int)tl, a, pass_tiles(p->log_n, logs, tl), st);
+    if (e == cudaSuccess)
+      e = L.pass((int)logs, mode, (int)tl, use_fused_tile(p, logs, tl), a, pass_tiles(p->log_n, logs, tl), st);
     if (e == cudaSuccess) e = timing_end(p, st);
     if (e != cudaSuccess) return cuda_status(e);
   }

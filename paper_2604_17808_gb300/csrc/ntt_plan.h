@@ -84,6 +84,8 @@ cudaError_t timing_begin(ntt_plan p, int pass, cudaStream_t st);
 cudaError_t timing_end(ntt_plan p, cudaStream_t st);
 
 ntt_status build_coset_tables(ntt_plan p, const U256 &s, cudaStream_t st);
+// Free all device tables of p and null their pointers (see ntt_plan.cu).
+void release_plan_tables(ntt_plan p);
 
 // matrix (tensor-core) path, ntt_matrix.cu
 bool matrix_path_available(ntt_plan p);

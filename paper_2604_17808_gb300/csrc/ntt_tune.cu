@@ -90,14 +90,7 @@ void save_file_locked() {
 
 void free_plan_memory(ntt_plan p) {
   release_matrix_resources(p);
-  for (void *ptr : p->allocations) cudaFree(ptr);
-  p->allocations.clear();
-  p->device_bytes = 0;
-  std::memset(p->dft_tw, 0, sizeof p->dft_tw);
-  std::memset(p->tw, 0, sizeof p->tw);
-  std::memset(p->pre, 0, sizeof p->pre);
-  std::memset(p->fac_coset, 0, sizeof p->fac_coset);
-  p->scratch = nullptr;
+  release_plan_tables(p);
 }
 
 // (Re)build plan p's tables for a butterfly choice.

@@ -1,8 +1,9 @@
 """The allocation-free batched entry point (ntt_batch_submit_static).
 
-Callers that cannot allocate device memory while they submit work -- code
-running while a stream is captured into a CUDA graph, or a service that
-reserved all its memory up front -- use this entry point: it runs the same
+Callers that cannot allocate device memory while they submit work -- a
+service that reserved all its memory up front, or a submitter on a latency
+path where cudaMalloc's implicit synchronisation would stall other streams --
+use this entry point: it runs the same
 batched kernel with its work-item table and counters in a fixed array the
 library keeps in device memory.  This test calls it through the C ABI and
 checks its outputs against the regular entry point (ntt_batch_submit) on two
