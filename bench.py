@@ -349,6 +349,20 @@ def measure_quotient(torch, N, stream, reps: int, log_n: int = 20, blowup_log: i
         N.ntt_plan_destroy(plan)
 
 
+def rns_words(limbs: np.ndarray, basis: dict) -> np.ndarray:
+    """Residues of [n, 4]-limb integers modulo the base-Q primes, as
+    [n, words_per_element] uint32 (input marshalling for ntt_rns_mul)."""
+    w32 = np.ascontiguousarray(limbs, dtype=np.uint64).view(np.uint32).reshape(-1, 8).astype(np.uint64)
+    out = np.zeros((w32.shape[0], basis["words_per_element"]), dtype=np.uint32)
+    for i, q in enumerate(basis["q"]):
+        q = np.uint64(q)
+        acc = np.zeros(w32.shape[0], dtype=np.uint64)
+        for w in range(8):
+            acc = (acc + (w32[:, w] % q) * np.uint64(pow(2, 32 * w, int(q)))) % q
+        out[:, i] = acc.astype(np.uint32)
+    return out
+
+
 def measure_modmul(torch, N, stream, count: int = 1 << 22, reps: int = 64) -> dict:
     """Montgomery products per second: per-thread carry chains (the library's
     form) vs 8 lanes per element with warp-shuffle carries."""
@@ -371,6 +385,27 @@ def measure_modmul(torch, N, stream, count: int = 1 << 22, reps: int = 64) -> di
         outs.append(z)
     res["identical"] = bool(torch.equal(outs[0], outs[1]))
     res["workload"] = f"{count} BLS12-381 elements x {reps} dependent Montgomery products"
+    # the paper's arithmetic: RNS lazy products, byte products on tcgen05
+    # (inputs: the same field elements as residues in base Q, 20 words each)
+    basis = N.ntt_rns_basis_get(FIELD)
+    xs = uniform_elements(FIELD, count, 77)
+    ys = uniform_elements(FIELD, count, 78)
+    rx = torch.from_numpy(rns_words(xs, basis).view(np.int32)).cuda()
+    ry = torch.from_numpy(rns_words(ys, basis).view(np.int32)).cuda()
+    rz = torch.empty_like(rx)
+    N.ntt_rns_mul(FIELD, rx, ry, rz, count, reps, stream)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    N.ntt_rns_mul(FIELD, rx, ry, rz, count, reps, stream)
+    stop.record(stream)
+    stop.synchronize()
+    ms = start.elapsed_time(stop)
+    res["rns_lazy_tensor_core"] = {"ms": round(ms, 4), "modmul_per_s": count * reps / (ms * 1e-3),
+                                   "vs_thread_carry_chains": round(res["thread_carry_chains"]["ms"] / ms, 3),
+                                   "device_error": N.ntt_rns_poll_error(FIELD),
+                                   "how": f"{len(basis['q'])} + {len(basis['p'])} residues of 31 bits, "
+                                          "two tcgen05 byte products per product (Alg. 1)"}
     return res
 
 

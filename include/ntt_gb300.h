@@ -381,6 +381,42 @@ ntt_status ntt_pointwise_quotient(ntt_field field, const void *d_a, const void *
                                   ntt_stream stream);
 
 /*
+ * The paper's RNS lazy modular multiplication (MORPH Sec. 3.2.3-3.2.4,
+ * Alg. 1 "MXU RNS Lazy") on the tensor cores, for measuring it against the
+ * 32-bit IMAD Montgomery product the transforms use.
+ *
+ * Representation: an element of F_M is carried as an integer in [0, L),
+ * L = (sum_i q_i + num_q) M, congruent to it ("lazy"), by its residues
+ * modulo the num_q primes q_i of base Q (the largest primes below 2^31,
+ * as many as give Q > 4 L^2).  Memory layout: words_per_element (20)
+ * uint32 per element, residue i in word i, the remaining words zero; 16-byte
+ * aligned device buffers.  A second base P of num_p primes (the next ones
+ * below, as many as give P > 2^20 L) serves the reduction.
+ *
+ * ntt_rns_mul computes, for every element e < count, out[e] = x[e] *
+ * y[e]^reps as a lazy element (congruent mod M, in [0, L)): each product
+ * is two 32-bit Montgomery products per residue, a quotient estimate
+ * scaled by 2^shift, a byte product (ByteDecompose, Einsum on tcgen05,
+ * ByteMerge) into base P, and an exact base extension (a second byte
+ * product) back to base Q.  Inputs must be canonical residues of an
+ * integer in [0, L).  Stream-ordered.  The first call per (device, field)
+ * builds and uploads the constant tables (synchronous, ~30 KB).  A device
+ * wait that runs out records NTT_ERR_TIMEOUT, read by ntt_rns_poll_error
+ * (which synchronises and clears it).
+ */
+typedef struct ntt_rns_basis {
+    uint32_t num_q, num_p;
+    uint32_t words_per_element;
+    uint32_t shift;
+    uint32_t q[24];
+    uint32_t p[16];
+} ntt_rns_basis;
+ntt_status ntt_rns_basis_get(ntt_field field, ntt_rns_basis *out);
+ntt_status ntt_rns_mul(ntt_field field, const void *d_x, const void *d_y, void *d_out, uint64_t count,
+                       uint32_t reps, ntt_stream stream);
+ntt_status ntt_rns_poll_error(ntt_field field, uint32_t *code);
+
+/*
  * Diagnostic: element-wise Montgomery product of device vectors,
  * out[i] = a[i] * b[i] * 2^-256 mod M, the field multiplication every
  * butterfly uses (the paper's "radix Mont" baseline, Sec. 2.3.2: 8 32-bit

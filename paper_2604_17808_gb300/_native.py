@@ -92,6 +92,9 @@ _SIGS = {
     "ntt_batch_debug_stall": (ctypes.c_int, [ctypes.c_int]),
     "ntt_batch_cache_clear": (ctypes.c_int, []),
     "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
+    "ntt_rns_basis_get": (ctypes.c_int, [ctypes.c_int, _VP]),
+    "ntt_rns_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _U32, _VP]),
+    "ntt_rns_poll_error": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_U32)]),
     "ntt_pointwise_quotient": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(_U64), _U32, _VP, _U64,
                                               _VP]),
     "ntt_field_mont_mul_rep": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _U32, ctypes.c_int, _VP]),
@@ -304,6 +307,29 @@ def ntt_pointwise_quotient(field, d_a, d_b, d_c, z_values, d_out, count: int, st
             arr[4 * j + k] = (v >> (64 * k)) & 0xFFFFFFFFFFFFFFFF
     _check(load().ntt_pointwise_quotient(_field(field), _ptr(d_a), _ptr(d_b), _ptr(d_c), arr, len(z), _ptr(d_out),
                                          int(count), _stream(stream)), "ntt_pointwise_quotient")
+
+
+class RnsBasis(ctypes.Structure):
+    _fields_ = [("num_q", _U32), ("num_p", _U32), ("words_per_element", _U32), ("shift", _U32),
+                ("q", _U32 * 24), ("p", _U32 * 16)]
+
+
+def ntt_rns_basis_get(field) -> dict:
+    b = RnsBasis()
+    _check(load().ntt_rns_basis_get(_field(field), ctypes.byref(b)), "ntt_rns_basis_get")
+    return {"q": list(b.q[: b.num_q]), "p": list(b.p[: b.num_p]), "words_per_element": b.words_per_element,
+            "shift": b.shift}
+
+
+def ntt_rns_mul(field, d_x, d_y, d_out, count: int, reps: int = 1, stream=None) -> None:
+    _check(load().ntt_rns_mul(_field(field), _ptr(d_x), _ptr(d_y), _ptr(d_out), int(count), int(reps),
+                              _stream(stream)), "ntt_rns_mul")
+
+
+def ntt_rns_poll_error(field) -> int:
+    code = _U32(0)
+    _check(load().ntt_rns_poll_error(_field(field), ctypes.byref(code)), "ntt_rns_poll_error")
+    return int(code.value)
 
 
 def ntt_plan_enable_timing(plan: int, enable: bool = True) -> None:
