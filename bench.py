@@ -272,6 +272,35 @@ def measure_2_24(torch, N, stream, steps: int) -> dict:
         N.ntt_plan_destroy(plan)
 
 
+def measure_large(torch, N, stream, steps: int, log_n: int = 28) -> dict:
+    """BLS12-381 Fr forward NTT at 2^28 (three passes, 8 GiB per vector).
+    The input is a seeded 2^20-element vector repeated (every entry a field
+    element; the kernels' work does not depend on the values)."""
+    plan = N.ntt_plan_create(FIELD, log_n)
+    try:
+        desc = N.ntt_plan_describe(plan)
+        base = to_dev(torch, uniform_elements(FIELD, 1 << 20, config_seed(3, 300)))
+        x = base.repeat(1 << (log_n - 20), 1)
+        y = torch.empty_like(x)
+        N.ntt_forward(plan, x, y, stream)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            N.ntt_forward(plan, x, y, stream)
+        stop.record(stream)
+        stop.synchronize()
+        ms = start.elapsed_time(stop) / steps
+        alg = transform_modmuls(log_n) * IMAD_PER_MODMUL
+        return {"workload": f"BLS12-381 Fr forward NTT, n=2^{log_n}, passes {desc['pass_log'][:desc['num_passes']]}",
+                "ms": round(ms, 3), "elements_per_s": (1 << log_n) / (ms * 1e-3),
+                "imad_roofline_frac": round(alg / (ms * 1e-3) / 1e12 / imad_peak_tops(), 4),
+                "device_bytes": desc["device_bytes"]}
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
 def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
     """The same workload on the matrix-form path (tensor-core passes)."""
     plan = N.ntt_plan_create(FIELD, log_n)
@@ -457,7 +486,7 @@ def measure_batched(torch, N, stream, reps: int) -> dict:
 
 
 def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int = 12, log_max: int = 24,
-                    seed: int = 0x5EED0005) -> dict:
+                    seed: int = 0x5EED0005, max_inflight: int = 8, max_batch_jobs: int = 16) -> dict:
     """Poisson arrivals of mixed forward/inverse/coset requests over both
     fields, log2 n uniform on {log_min..log_max}, through the serving runtime
     (host buffers in, host buffers out).  Per rate: p50/p99 latency
@@ -465,7 +494,7 @@ def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int
     import random
 
     server = N.ntt_server_create(memory_budget_bytes=64 << 30, min_log_n=log_min, max_log_n=log_max,
-                                 max_inflight=3, max_batch_jobs=64)
+                                 max_inflight=max_inflight, max_batch_jobs=max_batch_jobs)
     try:
         # one pinned input and output buffer per (field, size), reused by every request
         bufs = {}
@@ -506,7 +535,8 @@ def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int
                         "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)})
         stats = N.ntt_server_get_stats(server)
         return {"workload": f"Poisson arrivals, kinds forward/inverse/coset, fields BLS12-381/BN254, "
-                            f"log2 n uniform on {{{log_min}..{log_max}}}, 64 GiB budget, 3 streams",
+                            f"log2 n uniform on {{{log_min}..{log_max}}}, 64 GiB budget, {max_inflight} streams, "
+                            f"at most {max_batch_jobs} jobs per batch",
                 "rates": out, "batches": stats["batches"], "peak_device_bytes": stats["peak_device_bytes"],
                 "resident_bytes": stats["resident_bytes"]}
     finally:
@@ -645,6 +675,7 @@ def run_ours(args) -> None:
         e2e = measure_e2e(torch, N, host_inputs[0], max(8, args.steps // 2), log_n)
         if not args.quick:
             secondary = {"n_2_24_forward": measure_2_24(torch, N, stream, steps=max(3, args.steps // 4)),
+                         "n_2_28_forward": measure_large(torch, N, stream, steps=3),
                          "batched": measure_batched(torch, N, stream, reps=5),
                          "modmul": measure_modmul(torch, N, stream),
                          "quotient_step": measure_quotient(torch, N, stream, reps=5),
@@ -759,6 +790,20 @@ def run_serving_sweep(args) -> None:
     print(json.dumps({"metric": "serving p50/p99 latency and elements/s", "serving": res}), flush=True)
 
 
+def run_leg(args) -> None:
+    import torch
+
+    from paper_2604_17808_gb300 import _native as N
+
+    N.load(build_if_missing=True)
+    stream = torch.cuda.current_stream()
+    fn = {"modmul": lambda: measure_modmul(torch, N, stream),
+          "quotient": lambda: measure_quotient(torch, N, stream, reps=3),
+          "batched": lambda: measure_batched(torch, N, stream, reps=3),
+          "n_2_28": lambda: measure_large(torch, N, stream, steps=3)}[args.leg]
+    print(json.dumps({args.leg: fn()}), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -769,6 +814,8 @@ def main() -> None:
     ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
+    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28"],
+                    help="run only this secondary measurement and print its JSON (for profiling)")
     ap.add_argument("--rotate", type=int, default=ROTATE,
                     help="distinct input vectors the steps rotate over (default 8: larger than L2 at 2^20)")
     args = ap.parse_args()
@@ -776,6 +823,8 @@ def main() -> None:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg:
+        run_leg(args)
     elif args.serving:
         run_serving_sweep(args)
     else:
