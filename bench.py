@@ -301,6 +301,38 @@ def measure_large(torch, N, stream, steps: int, log_n: int = 28) -> dict:
         N.ntt_plan_destroy(plan)
 
 
+def measure_coset_2_24(torch, N, stream, steps: int) -> dict:
+    """BN254 Fr coset NTT at 2^24 (shift 5): the butterfly path against the
+    matrix (tensor-core) path on the same input, outputs compared."""
+    field, log_n = "bn254_fr", 24
+    plan = N.ntt_plan_create(field, log_n, coset=True)
+    try:
+        x = to_dev(torch, uniform_elements(field, 1 << log_n, config_seed(3)))
+        outs, ms = {}, {}
+        for path in ("butterfly", "matrix"):
+            N.ntt_plan_set_path(plan, path)
+            y = torch.empty_like(x)
+            N.ntt_coset_forward(plan, x, y, stream)
+            torch.cuda.synchronize()
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            for _ in range(steps):
+                N.ntt_coset_forward(plan, x, y, stream)
+            stop.record(stream)
+            stop.synchronize()
+            ms[path] = start.elapsed_time(stop) / steps
+            outs[path] = y
+        return {"workload": "BN254 Fr coset NTT, n=2^24, shift 5, butterfly vs matrix path",
+                "butterfly_ms": round(ms["butterfly"], 3), "matrix_ms": round(ms["matrix"], 3),
+                "butterfly_elements_per_s": (1 << log_n) / (ms["butterfly"] * 1e-3),
+                "matrix_elements_per_s": (1 << log_n) / (ms["matrix"] * 1e-3),
+                "identical": bool(torch.equal(outs["butterfly"], outs["matrix"])),
+                "device_error": N.ntt_plan_poll_error(plan)}
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
 def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
     """The same workload on the matrix-form path (tensor-core passes)."""
     plan = N.ntt_plan_create(FIELD, log_n)
@@ -676,6 +708,7 @@ def run_ours(args) -> None:
         if not args.quick:
             secondary = {"n_2_24_forward": measure_2_24(torch, N, stream, steps=max(3, args.steps // 4)),
                          "n_2_28_forward": measure_large(torch, N, stream, steps=3),
+                         "bn254_coset_2_24": measure_coset_2_24(torch, N, stream, steps=3),
                          "batched": measure_batched(torch, N, stream, reps=5),
                          "modmul": measure_modmul(torch, N, stream),
                          "quotient_step": measure_quotient(torch, N, stream, reps=5),
@@ -800,7 +833,8 @@ def run_leg(args) -> None:
     fn = {"modmul": lambda: measure_modmul(torch, N, stream),
           "quotient": lambda: measure_quotient(torch, N, stream, reps=3),
           "batched": lambda: measure_batched(torch, N, stream, reps=3),
-          "n_2_28": lambda: measure_large(torch, N, stream, steps=3)}[args.leg]
+          "n_2_28": lambda: measure_large(torch, N, stream, steps=3),
+          "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3)}[args.leg]
     print(json.dumps({args.leg: fn()}), flush=True)
 
 
@@ -814,7 +848,7 @@ def main() -> None:
     ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
-    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28"],
+    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24"],
                     help="run only this secondary measurement and print its JSON (for profiling)")
     ap.add_argument("--rotate", type=int, default=ROTATE,
                     help="distinct input vectors the steps rotate over (default 8: larger than L2 at 2^20)")

@@ -26,8 +26,17 @@ import numpy as np
 MODULI = {
     "bls12_381_fr": 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001,
     "bn254_fr": 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001,
+    # 377- and 753-bit NTT-friendly primes (c 2^32 + 1 above pi 2^(b-2))
+    "w377": 0x1921FB54442D18469898CC51701B839A252049C1114CF98E804177D4C76273644A29410F31C6809BBDF2BD500000001,
+    "w753": 0x1921FB54442D18469898CC51701B839A252049C1114CF98E804177D4C76273644A29410F31C6809BBDF2A33679A748636605614DBE4BE286E9FC26ADADAA3848BC90B6AECC4BCFD8DE89885D34C6FDAD617FEB96DE80D6FDBDCD300000001,
 }
-FIELD_NAMES = ("bls12_381_fr", "bn254_fr")
+FIELD_NAMES = ("bls12_381_fr", "bn254_fr", "w377", "w753")
+
+
+def words64_of(field) -> int:
+    """64-bit words of one element in memory: 4, 6 (377 bits) or 12 (753 bits)."""
+    bits = MODULI[_field_name(field)].bit_length()
+    return 4 if bits <= 256 else 6 if bits <= 384 else 12
 
 CONFIG_SEED_BASE = 0x5EED0000
 
@@ -58,23 +67,25 @@ def _field_name(field) -> str:
 
 
 def uniform_elements(field, n: int, seed: int) -> np.ndarray:
-    """n field elements uniform in [0, r), shape [n, 4] uint64 little-endian."""
+    """n field elements uniform in [0, r), shape [n, W] uint64 little-endian
+    (W = 4 for the 256-bit fields, 6 and 12 for the wide ones)."""
     r = MODULI[_field_name(field)]
     bits = r.bit_length()
-    top_mask = np.uint64((1 << (bits - 192)) - 1)
-    r_limbs = [np.uint64((r >> (64 * i)) & 0xFFFFFFFFFFFFFFFF) for i in range(4)]
-    out = np.empty((n, 4), dtype=np.uint64)
+    W = words64_of(field)
+    top_mask = np.uint64((1 << (bits - 64 * (W - 1))) - 1)
+    r_limbs = [np.uint64((r >> (64 * i)) & 0xFFFFFFFFFFFFFFFF) for i in range(W)]
+    out = np.empty((n, W), dtype=np.uint64)
     have = 0
     pos = 0
     while have < n:
         want = max(1024, int((n - have) * 1.4) + 64)
-        c = splitmix64(seed, 4 * want, start=pos).reshape(want, 4)
-        pos += 4 * want
-        c[:, 3] &= top_mask
+        c = splitmix64(seed, W * want, start=pos).reshape(want, W)
+        pos += W * want
+        c[:, W - 1] &= top_mask
         # lexicographic c < r from the top limb down
         lt = np.zeros(want, dtype=bool)
         eq = np.ones(want, dtype=bool)
-        for i in (3, 2, 1, 0):
+        for i in range(W - 1, -1, -1):
             lt |= eq & (c[:, i] < r_limbs[i])
             eq &= c[:, i] == r_limbs[i]
         acc = c[lt]

@@ -67,9 +67,33 @@ BN254_FR = Field(
     5,
     28,
 )
-FIELDS = {f.name: f for f in (BLS12_381_FR, BN254_FR)}
-# Index order used by the C ABI and by the C oracle.
-FIELD_BY_INDEX = (BLS12_381_FR, BN254_FR)
+# Wider fields for the paper's 377- and 753-bit rows (Sec. 4.3.1, Tab. 3
+# evaluates those precisions without naming the moduli).  Reading: the
+# smallest prime p = c 2^32 + 1, c odd, above floor(pi 2^(b-2)) (pseudo-random
+# high bits, 2-adicity exactly 32), generator = the smallest quadratic
+# non-residue, so g^((p-1)/N) is a primitive N-th root for N | 2^32.  The
+# pins recompute the rule with sympy/mpmath.
+W377 = Field(
+    "w377",
+    0x1921FB54442D18469898CC51701B839A252049C1114CF98E804177D4C76273644A29410F31C6809BBDF2BD500000001,
+    7,
+    32,
+)
+W753 = Field(
+    "w753",
+    0x1921FB54442D18469898CC51701B839A252049C1114CF98E804177D4C76273644A29410F31C6809BBDF2A33679A748636605614DBE4BE286E9FC26ADADAA3848BC90B6AECC4BCFD8DE89885D34C6FDAD617FEB96DE80D6FDBDCD300000001,
+    11,
+    32,
+)
+FIELDS = {f.name: f for f in (BLS12_381_FR, BN254_FR, W377, W753)}
+# Index order used by the C ABI and by the C oracle (which covers the first two).
+FIELD_BY_INDEX = (BLS12_381_FR, BN254_FR, W377, W753)
+
+
+def limbs_of_field(field) -> int:
+    """32-bit limbs of an element: 8 (<= 256 bits), 12 (377), 24 (753)."""
+    bits = get_field(field).modulus.bit_length()
+    return 8 if bits <= 256 else 12 if bits <= 384 else 24
 
 
 def get_field(field) -> Field:
@@ -244,17 +268,20 @@ def transform(field, kind: str, x, shift: int | None = None) -> list[int]:
 # ------------------------------------------------------- limb conversions
 
 
-def limbs_to_ints(a: np.ndarray) -> list[int]:
-    """[n, 4] uint64 little-endian limbs -> list of Python ints."""
-    a = np.ascontiguousarray(a, dtype=np.uint64).reshape(-1, 4)
+def limbs_to_ints(a: np.ndarray, words64: int = 4) -> list[int]:
+    """[n, words64] uint64 little-endian limbs -> list of Python ints."""
+    a = np.ascontiguousarray(a, dtype=np.uint64).reshape(-1, words64)
     out = []
     for row in a.tolist():
-        out.append(row[0] | (row[1] << 64) | (row[2] << 128) | (row[3] << 192))
+        v = 0
+        for i, w in enumerate(row):
+            v |= w << (64 * i)
+        out.append(v)
     return out
 
 
-def ints_to_limbs(v) -> np.ndarray:
-    """list of ints in [0, 2^256) -> [n, 4] uint64 little-endian limbs."""
+def ints_to_limbs(v, words64: int = 4) -> np.ndarray:
+    """list of ints in [0, 2^(64 words64)) -> [n, words64] uint64 limbs."""
     mask = (1 << 64) - 1
-    rows = [[(x >> (64 * i)) & mask for i in range(4)] for x in v]
-    return np.array(rows, dtype=np.uint64).reshape(-1, 4)
+    rows = [[(x >> (64 * i)) & mask for i in range(words64)] for x in v]
+    return np.array(rows, dtype=np.uint64).reshape(-1, words64)

@@ -108,6 +108,26 @@ def test_matrix_equals_butterfly_and_oracle_at_2_20(kind):
         N.ntt_plan_destroy(plan)
 
 
+def test_matrix_path_bn254_2_24_coset_matches_oracle_digest():
+    # the BN254 2^24 coset workload (shift 5) on the tensor-core path: eight
+    # passes of 8-point sub-transforms; stored oracle digest of the output
+    field, log_n = "bn254_fr", 24
+    x = uniform_elements(field, 1 << log_n, config_seed(3))
+    with open(os.path.join(HERE, "golden", "oracle_digests.json")) as fh:
+        want = [c for c in json.load(fh)["single"] if c["config"] == 3 and c["kind"] == "coset"][0]
+    assert hashlib.sha256(x.astype("<u8").tobytes()).hexdigest() == want["input_sha256"]
+    plan = matrix_plan(field, log_n)
+    try:
+        d_x = dev(x)
+        d_y = torch.empty_like(d_x)
+        N.ntt_execute(plan, "coset", d_x, d_y)
+        got = host(d_y)
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+    assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == want["output_sha256"]
+
+
 def test_matrix_path_in_place_and_custom_shift():
     field, log_n = "bn254_fr", 13
     f = O.get_field(field)

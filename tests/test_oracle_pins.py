@@ -37,15 +37,18 @@ from sympy.discrete.transforms import ntt as sympy_ntt
 
 import oracle
 from oracle import ntt_oracle as O
-from ntt_synth import uniform_elements
+from ntt_synth import uniform_elements, words64_of
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 FIELDS = [O.BLS12_381_FR, O.BN254_FR]
 FIELD_IDS = [f.name for f in FIELDS]
+WIDE = [O.W377, O.W753]
+ALL_FIELDS = FIELDS + WIDE
+ALL_IDS = [f.name for f in ALL_FIELDS]
 
 
 def rand_vec(field, n, seed):
-    return O.limbs_to_ints(uniform_elements(field.name, n, seed))
+    return O.limbs_to_ints(uniform_elements(field.name, n, seed), words64_of(field.name))
 
 
 # ------------------------------------------------------------- field data
@@ -235,10 +238,43 @@ ALL_PINS = [pin_sympy, pin_brute_force, pin_special_vectors, pin_convolution,
             pin_coset_horner, pin_roundtrip_linearity, pin_coset_inverse, pin_quotient_pipeline]
 
 
-@pytest.mark.parametrize("field", FIELDS, ids=FIELD_IDS)
+@pytest.mark.parametrize("field", ALL_FIELDS, ids=ALL_IDS)
 @pytest.mark.parametrize("pin", ALL_PINS, ids=[p.__name__ for p in ALL_PINS])
 def test_oracle_pin(pin, field):
+    if pin is pin_sympy and field in WIDE:
+        pytest.skip("sympy's NTT needs a factorisation of p - 1 (a 345/721-bit cofactor here)")
     assert pin(O, field)
+
+
+@pytest.mark.parametrize("field", WIDE, ids=[f.name for f in WIDE])
+def test_wide_field_follows_its_rule(field):
+    # the smallest prime c 2^32 + 1 (c odd) above floor(pi 2^(b-2)), b its bit
+    # length; the generator is the smallest quadratic non-residue
+    import mpmath
+
+    p = field.modulus
+    b = p.bit_length()
+    mpmath.mp.prec = b + 64
+    start = int(mpmath.floor(mpmath.pi * mpmath.mpf(2) ** (b - 2)))
+    assert p > start and (p - 1) % (1 << 32) == 0 and ((p - 1) >> 32) % 2 == 1
+    assert sympy.isprime(p)
+    c = (start >> 32) + 1
+    c += (c + 1) % 2
+    while (c << 32) + 1 < p:
+        assert not sympy.isprime((c << 32) + 1)
+        c += 2
+    g = field.generator
+    assert all(pow(a, (p - 1) // 2, p) == 1 for a in range(2, g))
+    assert pow(g, (p - 1) // 2, p) == p - 1
+    w = O.root_of_unity(field, 1 << 32)
+    assert pow(w, 1 << 31, p) == p - 1 and pow(w, 1 << 32, p) == 1
+
+
+@pytest.mark.parametrize("field", WIDE, ids=[f.name for f in WIDE])
+def test_wide_direct_definition_equals_radix2(field):
+    for n in (1 << k for k in range(1, 6)):
+        x = rand_vec(field, n, 7100 + n)
+        assert O.dft_direct(field, x) == O.ntt(field, x)
 
 
 @pytest.mark.parametrize("field", FIELDS, ids=FIELD_IDS)
