@@ -333,6 +333,31 @@ def measure_coset_2_24(torch, N, stream, steps: int) -> dict:
         N.ntt_plan_destroy(plan)
 
 
+def measure_wide(torch, N, stream, steps: int, log_n: int = 20) -> dict:
+    """Forward NTT at 2^20 over the 377- and 753-bit fields (the precisions of
+    the paper's wider rows), round trip checked."""
+    out = {}
+    for field in ("w377", "w753"):
+        x = to_dev(torch, uniform_elements(field, 1 << log_n, config_seed(2, 400)))
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        N.ntt_wide_transform(field, "forward", log_n, x, y, stream)
+        N.ntt_wide_transform(field, "inverse", log_n, y, z, stream)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            N.ntt_wide_transform(field, "forward", log_n, x, y, stream)
+        stop.record(stream)
+        stop.synchronize()
+        ms = start.elapsed_time(stop) / steps
+        out[field] = {"ms": round(ms, 4), "elements_per_s": (1 << log_n) / (ms * 1e-3),
+                      "round_trip_exact": bool(torch.equal(z, x))}
+    out["workload"] = f"forward NTT, n=2^{log_n}, 377- and 753-bit NTT-friendly primes"
+    return out
+
+
 def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
     """The same workload on the matrix-form path (tensor-core passes)."""
     plan = N.ntt_plan_create(FIELD, log_n)
@@ -709,6 +734,7 @@ def run_ours(args) -> None:
             secondary = {"n_2_24_forward": measure_2_24(torch, N, stream, steps=max(3, args.steps // 4)),
                          "n_2_28_forward": measure_large(torch, N, stream, steps=3),
                          "bn254_coset_2_24": measure_coset_2_24(torch, N, stream, steps=3),
+                         "wide_2_20": measure_wide(torch, N, stream, steps=10),
                          "batched": measure_batched(torch, N, stream, reps=5),
                          "modmul": measure_modmul(torch, N, stream),
                          "quotient_step": measure_quotient(torch, N, stream, reps=5),
@@ -834,7 +860,8 @@ def run_leg(args) -> None:
           "quotient": lambda: measure_quotient(torch, N, stream, reps=3),
           "batched": lambda: measure_batched(torch, N, stream, reps=3),
           "n_2_28": lambda: measure_large(torch, N, stream, steps=3),
-          "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3)}[args.leg]
+          "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3),
+          "wide": lambda: measure_wide(torch, N, stream, steps=10)}[args.leg]
     print(json.dumps({args.leg: fn()}), flush=True)
 
 
@@ -848,7 +875,7 @@ def main() -> None:
     ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
-    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24"],
+    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide"],
                     help="run only this secondary measurement and print its JSON (for profiling)")
     ap.add_argument("--rotate", type=int, default=ROTATE,
                     help="distinct input vectors the steps rotate over (default 8: larger than L2 at 2^20)")

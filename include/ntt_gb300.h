@@ -75,7 +75,12 @@ typedef enum ntt_status {
 
 typedef enum ntt_field {
     NTT_FIELD_BLS12_381_FR = 0, /* r = 0x73eda753...ffffffff00000001, 255 bits, 2-adicity 32, g = 7 */
-    NTT_FIELD_BN254_FR = 1      /* r = 0x30644e72...43e1f593f0000001, 254 bits, 2-adicity 28, g = 5 */
+    NTT_FIELD_BN254_FR = 1,     /* r = 0x30644e72...43e1f593f0000001, 254 bits, 2-adicity 28, g = 5 */
+    /* Wider fields for the paper's 377- and 753-bit rows (Sec. 4.3.1, Tab. 3),
+     * used through ntt_wide_transform only: the smallest primes c 2^32 + 1
+     * (c odd) above floor(pi 2^(b-2)), 2-adicity 32, generators 7 and 11. */
+    NTT_FIELD_W377 = 2,         /* 0x1921fb54...bdf2bd500000001, 377 bits; 48-byte elements */
+    NTT_FIELD_W753 = 3          /* 0x1921fb54...dcd300000001, 753 bits; 96-byte elements */
 } ntt_field;
 
 typedef enum ntt_kind {
@@ -379,6 +384,21 @@ ntt_status ntt_server_destroy(ntt_server server);
 ntt_status ntt_pointwise_quotient(ntt_field field, const void *d_a, const void *d_b, const void *d_c,
                                   const uint64_t *h_z, uint32_t z_len, void *d_out, uint64_t count,
                                   ntt_stream stream);
+
+/*
+ * Forward or inverse NTT of 2^log_n elements (1 <= log_n <= 24) over the
+ * 377- or 753-bit field: element i is 12 (resp. 24) little-endian uint32
+ * words at byte offset 48 i (resp. 96 i), standard form, canonical, natural
+ * order; device buffers 16-byte aligned; d_in == d_out allowed.  Same pass
+ * decomposition as the 256-bit transforms, with a generic-limb Montgomery
+ * product.  The first call for a (device, field, log_n) builds the tables
+ * on the device (synchronous; kept until the process exits).
+ * Stream-ordered.  NTT_ERR_UNSUPPORTED for other kinds or sizes.
+ */
+ntt_status ntt_wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, const void *d_in, void *d_out,
+                              ntt_stream stream);
+/* Bytes of one element of `field` in memory (32, 32, 48, 96). */
+ntt_status ntt_field_element_bytes(ntt_field field, uint32_t *bytes);
 
 /*
  * The paper's RNS lazy modular multiplication (MORPH Sec. 3.2.3-3.2.4,

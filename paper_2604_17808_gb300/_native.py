@@ -21,7 +21,7 @@ STATUS_NAMES = {
     0: "NTT_OK", 1: "NTT_ERR_INVALID_ARG", 2: "NTT_ERR_UNSUPPORTED", 3: "NTT_ERR_OOM",
     4: "NTT_ERR_CUDA", 5: "NTT_ERR_TIMEOUT", 6: "NTT_ERR_BUDGET", 7: "NTT_ERR_NO_DEVICE",
 }
-FIELD = {"bls12_381_fr": 0, "bn254_fr": 1}
+FIELD = {"bls12_381_fr": 0, "bn254_fr": 1, "w377": 2, "w753": 3}
 KIND = {"forward": 0, "inverse": 1, "coset": 2, "coset_inverse": 3}
 PATH = {"auto": 0, "butterfly": 1, "matrix": 2}
 HEADER = os.path.join(_build.ROOT, "include", "ntt_gb300.h")
@@ -93,6 +93,8 @@ _SIGS = {
     "ntt_batch_cache_clear": (ctypes.c_int, []),
     "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
     "ntt_rns_basis_get": (ctypes.c_int, [ctypes.c_int, _VP]),
+    "ntt_wide_transform": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _U32, _VP, _VP, _VP]),
+    "ntt_field_element_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_U32)]),
     "ntt_rns_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _U32, _VP]),
     "ntt_rns_poll_error": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_U32)]),
     "ntt_pointwise_quotient": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(_U64), _U32, _VP, _U64,
@@ -307,6 +309,17 @@ def ntt_pointwise_quotient(field, d_a, d_b, d_c, z_values, d_out, count: int, st
             arr[4 * j + k] = (v >> (64 * k)) & 0xFFFFFFFFFFFFFFFF
     _check(load().ntt_pointwise_quotient(_field(field), _ptr(d_a), _ptr(d_b), _ptr(d_c), arr, len(z), _ptr(d_out),
                                          int(count), _stream(stream)), "ntt_pointwise_quotient")
+
+
+def ntt_wide_transform(field, kind, log_n: int, d_in, d_out, stream=None) -> None:
+    _check(load().ntt_wide_transform(_field(field), _kind(kind), int(log_n), _ptr(d_in), _ptr(d_out),
+                                     _stream(stream)), "ntt_wide_transform")
+
+
+def ntt_field_element_bytes(field) -> int:
+    b = _U32(0)
+    _check(load().ntt_field_element_bytes(_field(field), ctypes.byref(b)), "ntt_field_element_bytes")
+    return int(b.value)
 
 
 class RnsBasis(ctypes.Structure):
