@@ -64,25 +64,34 @@ void host_double_mod(uint32_t x[NL], const uint32_t p[NL]) {
   }
 }
 
-template <int NL>
-WideConst<NL> make_const(const uint32_t p[NL], uint32_t gen) {
-  WideConst<NL> c{};
-  std::memcpy(c.p, p, sizeof c.p);
+template <int NL32>
+WideConst<NL32> make_const(const uint32_t p[NL32], uint32_t gen) {
+  constexpr int L = WideShape<NL32>::L;
+  WideConst<NL32> c{};
+  std::memcpy(c.p32, p, sizeof c.p32);
+  auto to29 = [&](uint32_t out[L], const uint32_t x[NL32]) {
+    for (int j = 0; j < L; ++j) {
+      const int bit = 29 * j, w = bit >> 5, sh = bit & 31;
+      const uint64_t lo = w < NL32 ? x[w] : 0u, hi = w + 1 < NL32 ? x[w + 1] : 0u;
+      out[j] = (uint32_t)(((hi << 32) | lo) >> sh) & kM29;
+    }
+  };
+  to29(c.p, p);
   uint32_t inv = 1;   // p^-1 mod 2^32 by Newton's iteration
   for (int t = 0; t < 5; ++t) inv *= 2u - p[0] * inv;
-  c.ninv = 0u - inv;
-  uint32_t x[NL] = {1};
-  for (int b = 0; b < 32 * NL; ++b) host_double_mod<NL>(x, p);   // R mod p
-  std::memcpy(c.one, x, sizeof c.one);
-  for (int b = 0; b < 32 * NL; ++b) host_double_mod<NL>(x, p);   // R^2 mod p
-  std::memcpy(c.r2, x, sizeof c.r2);
-  for (int j = 0; j < NL; ++j) c.exp_c[j] = j + 1 < NL ? p[j + 1] : 0u;   // (p - 1) >> 32 (p0 = 1)
+  c.ninv = (0u - inv) & kM29;
+  uint32_t x[NL32] = {1};
+  for (int b = 0; b < 29 * L; ++b) host_double_mod<NL32>(x, p);   // R mod p, R = 2^(29 L)
+  to29(c.one, x);
+  for (int b = 0; b < 29 * L; ++b) host_double_mod<NL32>(x, p);   // R^2 mod p
+  to29(c.r2, x);
+  for (int j = 0; j < NL32; ++j) c.exp_c[j] = j + 1 < NL32 ? p[j + 1] : 0u;   // (p - 1) >> 32 (p0 = 1)
   c.gen = gen;
   return c;
 }
 
 int limbs_of(int field) { return field == NTT_FIELD_W377 ? 12 : 24; }
-int tile_log(int field) { return field == NTT_FIELD_W377 ? WideTile<12>::kLog : WideTile<24>::kLog; }
+int tile_log(int field) { return field == NTT_FIELD_W377 ? WideShape<12>::kLog : WideShape<24>::kLog; }
 
 struct WidePlan {
   uint32_t log_n = 0, num_passes = 0;
@@ -100,15 +109,16 @@ std::map<std::tuple<int, int, uint32_t>, WidePlan *> g_wide_plans;   // (device,
 
 ntt_status cuda_w(cudaError_t e) { return cuda_status(e); }
 
-template <int NL>
-ntt_status gen_table(uint4 *out, uint32_t log_m, int dir, bool use_m_inv, uint32_t log_s, uint32_t log_mp,
-                     uint64_t count, int two_d, bool constant, uint32_t *kbuf, cudaStream_t st) {
-  wide_constants_kernel<NL><<<1, 1, 0, st>>>(kbuf, log_m);
-  const uint32_t *ladder = constant ? nullptr : kbuf + (dir ? 32 : 0) * NL;
-  const uint32_t *init = kbuf + (use_m_inv ? 64 : 65) * NL;
+template <int NL32>
+ntt_status gen_table(uint4 *out, uint32_t log_m, int dir, bool use_m_inv, uint32_t log_mp, uint64_t count, int two_d,
+                     bool constant, uint32_t *kbuf, cudaStream_t st) {
+  constexpr int L = WideShape<NL32>::L;
+  wide_constants_kernel<NL32><<<1, 1, 0, st>>>(kbuf, log_m);
+  const uint32_t *ladder = constant ? nullptr : kbuf + (dir ? 32 : 0) * L;
+  const uint32_t *init = kbuf + (use_m_inv ? 64 : 65) * L;
   uint64_t blocks = (count + 255) / 256;
   if (blocks > 152ull * 32) blocks = 152ull * 32;
-  wide_table_kernel<NL><<<(unsigned)(blocks ? blocks : 1), 256, 0, st>>>(out, log_s, log_mp, ladder, init, count, two_d);
+  wide_table_kernel<NL32><<<(unsigned)(blocks ? blocks : 1), 256, 0, st>>>(out, log_mp, ladder, init, count, two_d);
   return cuda_w(cudaGetLastError());
 }
 
@@ -124,17 +134,18 @@ ntt_status alloc_w(WidePlan *w, uint4 **out, uint64_t bytes) {
   return NTT_OK;
 }
 
-template <int NL>
+template <int NL32>
 ntt_status build_wide(int field, uint32_t log_n, WidePlan *w) {
+  constexpr int L = WideShape<NL32>::L, LP = WideShape<NL32>::LP;
   const uint32_t TL = (uint32_t)tile_log(field);
   const uint32_t P = (log_n + TL - 1) / TL;
   if (P > (uint32_t)kMaxPasses) return NTT_ERR_UNSUPPORTED;
   w->log_n = log_n;
   w->num_passes = P;
   for (uint32_t j = 0; j < P; ++j) w->pass_log[j] = log_n / P + (j < log_n % P ? 1 : 0);
-  const uint64_t eb = 4ull * NL;
+  const uint64_t eb = 4ull * LP;   // table entry: LP words of 29-bit limbs
   uint32_t *kbuf = nullptr;
-  if (cudaMalloc(&kbuf, 66 * 4 * NL) != cudaSuccess) return NTT_ERR_OOM;
+  if (cudaMalloc(&kbuf, 66 * 4 * L) != cudaSuccess) return NTT_ERR_OOM;
   w->allocs.push_back(kbuf);
   cudaStream_t st = nullptr;
   for (uint32_t j = 0; j < P; ++j) {
@@ -143,7 +154,7 @@ ntt_status build_wide(int field, uint32_t log_n, WidePlan *w) {
       if (w->dft_tw[dir][logs]) continue;
       const uint64_t cnt = logs ? (1ull << (logs - 1)) : 1;
       NTT_TRY_W(alloc_w(w, &w->dft_tw[dir][logs], cnt * eb));
-      NTT_TRY_W(gen_table<NL>(w->dft_tw[dir][logs], logs, dir, false, 0, 0, cnt, 0, false, kbuf, st));
+      NTT_TRY_W(gen_table<NL32>(w->dft_tw[dir][logs], logs, dir, false, 0, cnt, 0, false, kbuf, st));
     }
   }
   uint32_t log_m = w->pass_log[0];
@@ -152,21 +163,21 @@ ntt_status build_wide(int field, uint32_t log_n, WidePlan *w) {
     log_m += logs;
     for (int dir = 0; dir < 2; ++dir) {
       NTT_TRY_W(alloc_w(w, &w->tw[dir][j], (1ull << log_m) * eb));
-      NTT_TRY_W(gen_table<NL>(w->tw[dir][j], log_m, dir, dir == 1 && j == P - 1, logs, log_mp, 1ull << log_m, 1,
-                              false, kbuf, st));
+      NTT_TRY_W(gen_table<NL32>(w->tw[dir][j], log_m, dir, dir == 1 && j == P - 1, log_mp, 1ull << log_m, 1, false,
+                                kbuf, st));
     }
   }
   if (P == 1) {   // single-pass inverse: N^-1 as the pass-0 multiplier
     NTT_TRY_W(alloc_w(w, &w->pre_inv, (1ull << log_n) * eb));
-    NTT_TRY_W(gen_table<NL>(w->pre_inv, log_n, 0, true, 0, 0, 1ull << log_n, 0, true, kbuf, st));
+    NTT_TRY_W(gen_table<NL32>(w->pre_inv, log_n, 0, true, 0, 1ull << log_n, 0, true, kbuf, st));
   }
-  if (P > 1) NTT_TRY_W(alloc_w(w, &w->scratch, (1ull << log_n) * eb));
+  if (P > 1) NTT_TRY_W(alloc_w(w, &w->scratch, (1ull << log_n) * 4ull * NL32));   // memory-layout elements
   return cuda_w(cudaDeviceSynchronize());
 }
 
 template <int NL, int LOGS>
 cudaError_t wide_launch(int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
-  const int smem = WideTile<NL>::kBytes;
+  const int smem = WideShape<NL>::kBytes;
   switch (mode) {
     case kModeInner: wide_pass_kernel<NL, LOGS, kModeInner><<<(unsigned)tiles, 256, smem, st>>>(a); break;
     case kModeFirst: wide_pass_kernel<NL, LOGS, kModeFirst><<<(unsigned)tiles, 256, smem, st>>>(a); break;
@@ -177,7 +188,7 @@ cudaError_t wide_launch(int mode, const PassArgs &a, uint64_t tiles, cudaStream_
 
 template <int NL, int LOGS>
 cudaError_t wide_attr() {
-  const int smem = WideTile<NL>::kBytes;
+  const int smem = WideShape<NL>::kBytes;
   cudaError_t e = cudaFuncSetAttribute(wide_pass_kernel<NL, LOGS, kModeInner>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
@@ -199,7 +210,7 @@ cudaError_t wide_set_attrs() {
   if (e == cudaSuccess) e = wide_attr<NL, 7>();
   if (e == cudaSuccess) e = wide_attr<NL, 8>();
   if (e == cudaSuccess) e = wide_attr<NL, 9>();
-  if constexpr (WideTile<NL>::kLog >= 10) {
+  if constexpr (WideShape<NL>::kLog >= 10) {
     if (e == cudaSuccess) e = wide_attr<NL, 10>();
   }
   return e;
@@ -218,7 +229,7 @@ cudaError_t wide_dispatch(int logs, int mode, const PassArgs &a, uint64_t tiles,
     case 8: return wide_launch<NL, 8>(mode, a, tiles, st);
     case 9: return wide_launch<NL, 9>(mode, a, tiles, st);
     case 10:
-      if constexpr (WideTile<NL>::kLog >= 10) return wide_launch<NL, 10>(mode, a, tiles, st);
+      if constexpr (WideShape<NL>::kLog >= 10) return wide_launch<NL, 10>(mode, a, tiles, st);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
