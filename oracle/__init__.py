@@ -10,6 +10,10 @@ Two independent implementations of the same definition (MORPH Sec. 2.3.1):
     textbook radix-2 evaluation of it);
   * ``ntt_oracle.c`` -- plain C, 4 x 64-bit limbs, HAC 14.36 Montgomery, used
     where Python is too slow (2^20 and 2^24 elements), loaded by ``c_oracle()``.
+
+Companions: ``rns_oracle`` (the paper's RNS lazy modular multiplication) and
+``msm_oracle`` (multi-scalar multiplication on BN254 G1: the definition and
+the paper's Layout-Stationary Pippenger).
 """
 
 from __future__ import annotations

@@ -46,6 +46,10 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.ntt_plan_create(ctypes.byref(h), 0, 0, 0) == 2
     assert lib.ntt_plan_create(ctypes.byref(h), 0, 29, 0) == 2
     assert lib.ntt_plan_create(ctypes.byref(h), 1, 29, 0) == 2  # BN254 2-adicity is 28
+    assert lib.ntt_plan_create(ctypes.byref(h), 2, 12, 0) == 1  # the wide fields use ntt_wide_transform
+    b = ctypes.c_uint32(0)
+    assert lib.ntt_field_element_bytes(3, ctypes.byref(b)) == 0 and b.value == 96
+    assert lib.ntt_field_element_bytes(4, ctypes.byref(b)) == 1
     assert h.value is None
 
 
