@@ -358,6 +358,66 @@ def measure_wide(torch, N, stream, steps: int, log_n: int = 20) -> dict:
     return out
 
 
+# MORPH's MSM latencies for the 256-bit curve (TPUv6e-8, Tab. 4), in ms
+PAPER_MSM_MS = {22: 1.61, 24: 6.42, 26: 25.64}
+MSM_CONFIG = 6  # seeds of the MSM inputs (shared with the tests)
+
+
+def msm_inputs(torch, N, stream, n: int):
+    """Scalars uniform in [0, r); points t_n G from the library's fixed-base
+    generator (t_n seeded uniform), so that the result has a closed form."""
+    d_s = to_dev(torch, uniform_elements("bn254_fr", n, config_seed(MSM_CONFIG)))
+    d_t = to_dev(torch, uniform_elements("bn254_fr", n, config_seed(MSM_CONFIG, 1)))
+    pts = torch.empty((n, 8), dtype=torch.int64, device=d_s.device)
+    N.msm_fixed_base("bn254_g1", d_t, n, pts, stream)
+    torch.cuda.synchronize()
+    del d_t
+    return d_s, pts
+
+
+def measure_msm(torch, N, stream, reps: int, log_sizes=(22, 24)) -> dict:
+    """Multi-scalar multiplication on BN254 G1 (Algorithm 2, LS-PPG): the
+    whole call (point conversion, bucketize, accumulation, tree reduction,
+    window merge) timed with CUDA events; the paper's sizes 2^22..2^26."""
+    out = {}
+    peak = imad_peak_tops()
+    for lg in log_sizes:
+        n = 1 << lg
+        d_s, pts = msm_inputs(torch, N, stream, n)
+        plan = N.msm_plan_create("bn254_g1", n, 0)
+        info = N.msm_plan_info(plan)
+        res = torch.empty(8, dtype=torch.int64, device=d_s.device)
+        N.msm_execute(plan, d_s, pts, n, res, stream)
+        torch.cuda.synchronize()
+        first = res.clone()
+        times = []
+        for _ in range(reps):
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            N.msm_execute(plan, d_s, pts, n, res, stream)
+            stop.record(stream)
+            stop.synchronize()
+            times.append(start.elapsed_time(stop))
+        ms = float(np.median(times))
+        c, K = info["window_bits"], info["num_windows"]
+        # algorithmic products: one 10-product mixed addition per point and
+        # window, about 26 per bucket in the reduction tree
+        modmuls = K * n * 10 + K * (1 << c) * 26
+        achieved = modmuls * IMAD_PER_MODMUL / (ms * 1e-3) / 1e12
+        out[f"n_2_{lg}"] = {"ms": round(ms, 3), "points_per_s": n / (ms * 1e-3), "window_bits": c, "windows": K,
+                            "segment_length": info["segment_length"], "plan_device_gb":
+                            round(info["device_bytes"] / 1e9, 2), "algorithmic_modmuls": modmuls,
+                            "imad_frac": round(achieved / peak, 4), "repeatable": bool(torch.equal(res, first)),
+                            "device_error": N.msm_poll_error(plan), "paper_tpu_ms": PAPER_MSM_MS.get(lg)}
+        N.msm_plan_destroy(plan)
+        del d_s, pts
+        torch.cuda.empty_cache()
+    out["workload"] = ("MSM on BN254 G1 by Layout-Stationary Pippenger, scalars uniform < r, points t_n G "
+                       "(seeded), result checked against the closed form in the tests")
+    return out
+
+
 def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
     """The same workload on the matrix-form path (tensor-core passes)."""
     plan = N.ntt_plan_create(FIELD, log_n)
@@ -738,6 +798,7 @@ def run_ours(args) -> None:
                          "batched": measure_batched(torch, N, stream, reps=5),
                          "modmul": measure_modmul(torch, N, stream),
                          "quotient_step": measure_quotient(torch, N, stream, reps=5),
+                         "msm_bn254": measure_msm(torch, N, stream, reps=3),
                          "serving": measure_serving(torch, N, rates=(100, 1000, 5000), seconds=0.5, min_jobs=40)}
         if world == 1 and not args.no_cpu:
             cpu = cpu_baseline(host_inputs[0])
@@ -861,7 +922,8 @@ def run_leg(args) -> None:
           "batched": lambda: measure_batched(torch, N, stream, reps=3),
           "n_2_28": lambda: measure_large(torch, N, stream, steps=3),
           "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3),
-          "wide": lambda: measure_wide(torch, N, stream, steps=10)}[args.leg]
+          "wide": lambda: measure_wide(torch, N, stream, steps=10),
+          "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=(22, 24, 26))}[args.leg]
     print(json.dumps({args.leg: fn()}), flush=True)
 
 
@@ -875,7 +937,7 @@ def main() -> None:
     ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
-    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide"],
+    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide", "msm"],
                     help="run only this secondary measurement and print its JSON (for profiling)")
     ap.add_argument("--rotate", type=int, default=ROTATE,
                     help="distinct input vectors the steps rotate over (default 8: larger than L2 at 2^20)")

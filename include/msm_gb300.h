@@ -1,0 +1,95 @@
+/*
+ * msm_gb300.h -- C ABI of the multi-scalar multiplication (MSM) of the
+ * GB300 (sm_103a) library.
+ *
+ * The operation (MORPH, Sec. 2.3.1, the MSM definition; computed by the
+ * paper's Layout-Stationary Pippenger, Algorithm 2): for N scalars S_n and
+ * N points P_n of an elliptic-curve group,
+ *
+ *     MSM = sum_{n<N} S_n P_n.
+ *
+ * The result is a group element, so it is exact and unique.
+ *
+ * Curve: BN254 G1, y^2 = x^3 + 3 over F_q,
+ *   q = 0x30644e72e131a029b85045b68181585d97816a916871ca8d3c208c16d87cfd47,
+ * a group of prime order r = the BN254 scalar-field modulus (ntt_gb300.h's
+ * NTT_FIELD_BN254_FR), generator G = (1, 2).
+ *
+ * Data layout (device buffers, 32-byte aligned):
+ *   scalars  N x 32 bytes: four little-endian uint64 limbs, canonical in [0, r);
+ *   points   N x 64 bytes: affine x then y, each four little-endian uint64
+ *            limbs, standard (not Montgomery) form, canonical in [0, q); the
+ *            point at infinity is encoded as x = y = 0 (not a curve point);
+ *   result   64 bytes, same encoding as one point.
+ *
+ * Ownership: the caller owns scalars, points and result.  A plan owns its
+ * device scratch (a Montgomery copy of the points, the bucket index arrays,
+ * segment sums and the reduction tree), allocated by msm_plan_create on the
+ * current device and freed by msm_plan_destroy; msm_plan_info reports its
+ * size.
+ *
+ * Streams: msm_execute only enqueues work on `stream` and returns.  The
+ * scratch is shared by every call on a plan, so calls on one plan must be
+ * ordered (one stream, or one plan per stream).
+ *
+ * Errors: NTT_ERR_INVALID_ARG for a NULL plan or buffer, a misaligned
+ * buffer, an unknown curve or n > max_n; NTT_ERR_UNSUPPORTED for max_n above
+ * MSM_MAX_POINTS, window_bits outside [1, 22] (0 = automatic), or a plan whose
+ * bucket index count (max_n x windows) would not fit 32 bits;
+ * NTT_ERR_OOM / NTT_ERR_CUDA / NTT_ERR_NO_DEVICE as in ntt_gb300.h.  Input
+ * checks run on the device: a point that is not canonical or not on the
+ * curve sets MSM_ERR_POINT and is treated as the point at infinity; a scalar
+ * >= r sets MSM_ERR_SCALAR (its digits are still used).  msm_poll_error
+ * reads and clears these bits (it synchronises with the device).
+ */
+#ifndef MSM_GB300_H
+#define MSM_GB300_H
+
+#include "ntt_gb300.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum msm_curve {
+    MSM_CURVE_BN254_G1 = 0
+} msm_curve;
+
+#define MSM_MAX_POINTS (1ull << 28)
+#define MSM_ERR_POINT 1u  /* a point not canonical or not on the curve */
+#define MSM_ERR_SCALAR 2u /* a scalar >= r */
+
+typedef struct msm_plan_s *msm_plan;
+
+typedef struct msm_plan_desc {
+    uint64_t max_n;          /* largest n accepted by msm_execute */
+    uint32_t window_bits;    /* c: digits of c bits, 2^c buckets per window */
+    uint32_t num_windows;    /* K = ceil(254 / c) */
+    uint32_t segment_length; /* points summed by one thread before the tree */
+    uint32_t reserved;
+    uint64_t device_bytes;   /* scratch owned by the plan */
+} msm_plan_desc;
+
+/* Plan for up to max_n points.  window_bits = 0 picks c from max_n. */
+ntt_status msm_plan_create(msm_plan *out, msm_curve curve, uint64_t max_n, uint32_t window_bits);
+ntt_status msm_plan_info(msm_plan plan, msm_plan_desc *out);
+/* Synchronises the device, then frees the plan's scratch. */
+ntt_status msm_plan_destroy(msm_plan plan);
+
+/* result = sum_{n < count} scalars[n] points[n]; count may be 0 (result = O). */
+ntt_status msm_execute(msm_plan plan, const void *d_scalars, const void *d_points, uint64_t count,
+                       void *d_result, ntt_stream stream);
+ntt_status msm_poll_error(msm_plan plan, uint32_t *flags);
+
+/* Fixed-base generation of inputs: points[n] = scalars[n] G (affine, standard
+ * form; a zero scalar gives the point at infinity), any scalars < 2^256.
+ * The first call on a device builds and keeps a 512 KiB comb table of
+ * multiples of G (it synchronises `stream` once). */
+ntt_status msm_fixed_base(msm_curve curve, const void *d_scalars, uint64_t count, void *d_points,
+                          ntt_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSM_GB300_H */

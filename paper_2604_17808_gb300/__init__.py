@@ -5,7 +5,9 @@ include/ntt_gb300.h); this package is its thin Python binding:
 
   * ``_native``  -- ctypes wrappers named like the C calls;
   * ``_build``   -- the nvcc build of the library;
-  * ``Plan``     -- a small owner object over a plan handle for torch users.
+  * ``Plan``     -- a small owner object over a plan handle for torch users;
+  * ``MsmPlan``  -- the same for the multi-scalar multiplication on BN254 G1
+                    (C ABI in include/msm_gb300.h).
 
 Importing the package does not load CUDA; the first call does, and raises if
 the library has not been built.
@@ -17,8 +19,15 @@ from . import _build, _native  # noqa: F401
 from ._native import (  # noqa: F401
     FIELD,
     KIND,
+    CURVE,
     PATH,
     NttError,
+    msm_execute,
+    msm_fixed_base,
+    msm_plan_create,
+    msm_plan_destroy,
+    msm_plan_info,
+    msm_poll_error,
     ntt_batch_submit,
     ntt_coset_forward,
     ntt_coset_inverse,
@@ -88,3 +97,52 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class MsmPlan:
+    """Owns one msm_plan handle.  Scalars: torch int64 [n, 4]; points: [n, 8]
+    (affine x limbs then y limbs, standard form, (0, 0) = infinity); the
+    result is one point, [8]."""
+
+    def __init__(self, max_n: int, window_bits: int = 0, curve: str = "bn254_g1"):
+        self.curve = curve
+        self.max_n = int(max_n)
+        self.handle = msm_plan_create(curve, self.max_n, window_bits)
+
+    def info(self) -> dict:
+        return msm_plan_info(self.handle)
+
+    def execute(self, scalars, points, out=None, count: int | None = None, stream=None):
+        n = scalars.shape[0] if count is None else int(count)
+        if out is None:
+            out = scalars.new_empty((8,))
+        msm_execute(self.handle, scalars, points, n, out, stream)
+        return out
+
+    def poll_error(self) -> int:
+        return msm_poll_error(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            msm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fixed_base_points(scalars, out=None, stream=None):
+    """points[n] = scalars[n] G on BN254 G1 (input generation for MSM)."""
+    if out is None:
+        out = scalars.new_empty((scalars.shape[0], 8))
+    msm_fixed_base("bn254_g1", scalars, scalars.shape[0], out, stream)
+    return out

@@ -25,6 +25,8 @@ FIELD = {"bls12_381_fr": 0, "bn254_fr": 1, "w377": 2, "w753": 3}
 KIND = {"forward": 0, "inverse": 1, "coset": 2, "coset_inverse": 3}
 PATH = {"auto": 0, "butterfly": 1, "matrix": 2}
 HEADER = os.path.join(_build.ROOT, "include", "ntt_gb300.h")
+HEADERS = (HEADER, os.path.join(_build.ROOT, "include", "msm_gb300.h"))
+CURVE = {"bn254_g1": 0}
 
 
 class NttError(RuntimeError):
@@ -57,6 +59,12 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("path", ctypes.c_uint32), ("num_passes", ctypes.c_uint32), ("pass_log", ctypes.c_uint32 * 4),
                 ("tile_log", ctypes.c_uint32 * 4), ("candidates", ctypes.c_uint32), ("best_ms", ctypes.c_double),
                 ("default_ms", ctypes.c_double)]
+
+
+class MsmPlanDesc(ctypes.Structure):
+    _fields_ = [("max_n", ctypes.c_uint64), ("window_bits", ctypes.c_uint32), ("num_windows", ctypes.c_uint32),
+                ("segment_length", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64)]
 
 
 class Job(ctypes.Structure):
@@ -111,6 +119,12 @@ _SIGS = {
     "ntt_server_release": (ctypes.c_int, [_VP, _U64]),
     "ntt_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ServerStats)]),
     "ntt_server_destroy": (ctypes.c_int, [_VP]),
+    "msm_plan_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _U64, _U32]),
+    "msm_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(MsmPlanDesc)]),
+    "msm_plan_destroy": (ctypes.c_int, [_VP]),
+    "msm_execute": (ctypes.c_int, [_VP, _VP, _VP, _U64, _VP, _VP]),
+    "msm_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
+    "msm_fixed_base": (ctypes.c_int, [ctypes.c_int, _VP, _U64, _VP, _VP]),
     "ntt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ntt_version": (_U32, []),
 }
@@ -140,11 +154,14 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
 
 
 def declared_functions() -> list[str]:
-    """Names of the functions include/ntt_gb300.h declares."""
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ntt_[a-z0-9_]+)\s*\(", text, flags=re.M)
-    return sorted(set(names))
+    """Names of the functions the headers under include/ declare."""
+    names: set[str] = set()
+    for header in HEADERS:
+        text = open(header).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*((?:ntt|msm)_[a-z0-9_]+)\s*\(",
+                                text, flags=re.M))
+    return sorted(names)
 
 
 def _ptr(x) -> int | None:
@@ -406,6 +423,43 @@ def ntt_server_destroy(server: int) -> None:
 def ntt_field_mont_mul_rep(field, d_a, d_b, d_out, count: int, reps: int, variant: int, stream=None) -> None:
     _check(load().ntt_field_mont_mul_rep(_field(field), _ptr(d_a), _ptr(d_b), _ptr(d_out), int(count), int(reps),
                                          int(variant), _stream(stream)), "ntt_field_mont_mul_rep")
+
+
+def _curve(c) -> int:
+    return CURVE[c] if isinstance(c, str) else int(c)
+
+
+def msm_plan_create(curve, max_n: int, window_bits: int = 0) -> int:
+    h = _VP()
+    _check(load().msm_plan_create(ctypes.byref(h), _curve(curve), int(max_n), int(window_bits)), "msm_plan_create")
+    return int(h.value)
+
+
+def msm_plan_info(plan: int) -> dict:
+    d = MsmPlanDesc()
+    _check(load().msm_plan_info(plan, ctypes.byref(d)), "msm_plan_info")
+    return {"max_n": d.max_n, "window_bits": d.window_bits, "num_windows": d.num_windows,
+            "segment_length": d.segment_length, "device_bytes": d.device_bytes}
+
+
+def msm_plan_destroy(plan: int) -> None:
+    _check(load().msm_plan_destroy(plan), "msm_plan_destroy")
+
+
+def msm_execute(plan: int, d_scalars, d_points, count: int, d_result, stream=None) -> None:
+    _check(load().msm_execute(plan, _ptr(d_scalars), _ptr(d_points), int(count), _ptr(d_result), _stream(stream)),
+           "msm_execute")
+
+
+def msm_poll_error(plan: int) -> int:
+    flags = _U32(0)
+    _check(load().msm_poll_error(plan, ctypes.byref(flags)), "msm_poll_error")
+    return int(flags.value)
+
+
+def msm_fixed_base(curve, d_scalars, count: int, d_points, stream=None) -> None:
+    _check(load().msm_fixed_base(_curve(curve), _ptr(d_scalars), int(count), _ptr(d_points), _stream(stream)),
+           "msm_fixed_base")
 
 
 def ntt_status_string(status: int) -> str:

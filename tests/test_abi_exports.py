@@ -69,3 +69,28 @@ def test_no_gpu_is_reported_loudly(lib):
     assert lib.ntt_plan_create(ctypes.byref(h), 0, 12, 0) == 7  # NTT_ERR_NO_DEVICE
     with pytest.raises(_native.NttError):
         _native.ntt_plan_create("bls12_381_fr", 12)
+
+
+def test_msm_arguments_are_checked_without_touching_the_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.msm_plan_create(None, 0, 16, 0) == 1
+    assert lib.msm_plan_create(ctypes.byref(h), 1, 16, 0) == 1          # unknown curve
+    assert lib.msm_plan_create(ctypes.byref(h), 0, (1 << 28) + 1, 0) == 2  # above MSM_MAX_POINTS
+    assert lib.msm_plan_create(ctypes.byref(h), 0, 16, 23) == 2         # window too wide
+    assert lib.msm_plan_create(ctypes.byref(h), 0, 1 << 25, 1) == 2     # 254 windows x 2^25 > 2^32 indices
+    assert h.value is None
+    assert lib.msm_execute(None, None, None, 0, None, None) == 1
+    assert lib.msm_plan_destroy(None) == 1
+    assert lib.msm_plan_info(None, None) == 1
+    assert lib.msm_poll_error(None, None) == 1
+    assert lib.msm_fixed_base(3, None, 4, None, None) == 1
+    assert lib.msm_fixed_base(0, None, 0, None, None) == 0              # nothing to do
+    assert lib.msm_fixed_base(0, None, 4, None, None) == 1
+
+
+def test_msm_no_gpu_is_reported_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.msm_plan_create(ctypes.byref(h), 0, 1024, 0) == 7  # NTT_ERR_NO_DEVICE
