@@ -402,8 +402,8 @@ def measure_msm(torch, N, stream, reps: int, log_sizes=(22, 24)) -> dict:
         ms = float(np.median(times))
         c, K = info["window_bits"], info["num_windows"]
         # algorithmic products: one 10-product mixed addition per point and
-        # window, about 26 per bucket in the reduction tree
-        modmuls = K * n * 10 + K * (1 << c) * 26
+        # window, about 26 per bucket (2^(c-1) per window) in the reduction tree
+        modmuls = K * n * 10 + K * (1 << (c - 1)) * 26
         achieved = modmuls * IMAD_PER_MODMUL / (ms * 1e-3) / 1e12
         out[f"n_2_{lg}"] = {"ms": round(ms, 3), "points_per_s": n / (ms * 1e-3), "window_bits": c, "windows": K,
                             "segment_length": info["segment_length"], "plan_device_gb":

@@ -39,8 +39,9 @@
  * NTT_ERR_OOM / NTT_ERR_CUDA / NTT_ERR_NO_DEVICE as in ntt_gb300.h.  Input
  * checks run on the device: a point that is not canonical or not on the
  * curve sets MSM_ERR_POINT and is treated as the point at infinity; a scalar
- * >= r sets MSM_ERR_SCALAR (its digits are still used).  msm_poll_error
- * reads and clears these bits (it synchronises with the device).
+ * >= r sets MSM_ERR_SCALAR (the result stays exact for scalars below 2^254
+ * and is unspecified above).  msm_poll_error reads and clears these bits
+ * (it synchronises with the device).
  */
 #ifndef MSM_GB300_H
 #define MSM_GB300_H
@@ -63,14 +64,15 @@ typedef struct msm_plan_s *msm_plan;
 
 typedef struct msm_plan_desc {
     uint64_t max_n;          /* largest n accepted by msm_execute */
-    uint32_t window_bits;    /* c: digits of c bits, 2^c buckets per window */
-    uint32_t num_windows;    /* K = ceil(254 / c) */
+    uint32_t window_bits;    /* c: signed digits of c bits, 2^(c-1) buckets per window */
+    uint32_t num_windows;    /* K = ceil(255 / c) */
     uint32_t segment_length; /* points summed by one thread before the tree */
     uint32_t reserved;
     uint64_t device_bytes;   /* scratch owned by the plan */
 } msm_plan_desc;
 
-/* Plan for up to max_n points.  window_bits = 0 picks c from max_n. */
+/* Plan for up to max_n points.  window_bits = 0 picks c from max_n; for
+ * window_bits = 1 every window holds one bucket. */
 ntt_status msm_plan_create(msm_plan *out, msm_curve curve, uint64_t max_n, uint32_t window_bits);
 ntt_status msm_plan_info(msm_plan plan, msm_plan_desc *out);
 /* Synchronises the device, then frees the plan's scratch. */

@@ -32,6 +32,35 @@ static_assert(FieldBn254Fq::P0 * (0u - FieldBn254Fq::NP) == 1u, "NP");
 
 using Fq = FieldBn254Fq;
 
+// The same product as an out-of-line call with the operands passed by value
+// (they travel in registers; no stack frame).  The mixed addition of the
+// bucket-accumulation loop uses it: one shared copy of the product's ~300
+// instructions instead of ten inlined copies keeps the loop inside the
+// instruction cache (measured on GB300: the whole MSM at 2^24 points 9%
+// faster).  The other formulas keep the inlined product, which measured
+// faster for them.
+struct FeV {
+  uint32_t v[8];
+};
+
+__device__ __noinline__ FeV fq_mul_call(FeV a, FeV b) {
+  FeV r;
+  mont_mul<Fq>(r.v, a.v, b.v);
+  return r;
+}
+
+__device__ __forceinline__ void fq_mul_small(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+  FeV x, y;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    x.v[j] = a[j];
+    y.v[j] = b[j];
+  }
+  const FeV z = fq_mul_call(x, y);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = z.v[j];
+}
+
 struct PointXyzz {
   uint32_t X[8], Y[8], ZZ[8], ZZZ[8];
 };
@@ -124,27 +153,27 @@ __device__ __forceinline__ void xyzz_madd(PointXyzz &acc, const uint32_t x2[8], 
     return;
   }
   uint32_t P[8], R[8], PP[8], PPP[8], Q[8];
-  mont_mul<Fq>(P, x2, acc.ZZ);
+  fq_mul_small(P, x2, acc.ZZ);
   sub_mod<Fq>(P, P, acc.X);       // P = U2 - X1
-  mont_mul<Fq>(R, y2, acc.ZZZ);
+  fq_mul_small(R, y2, acc.ZZZ);
   sub_mod<Fq>(R, R, acc.Y);       // R = S2 - Y1
   if (fe_is_zero(P)) {
     if (fe_is_zero(R)) xyzz_mdbl(acc, x2, y2);  // same point
     else xyzz_set_inf(acc);                     // opposite points
     return;
   }
-  mont_mul<Fq>(PP, P, P);
-  mont_mul<Fq>(PPP, P, PP);
-  mont_mul<Fq>(acc.ZZ, acc.ZZ, PP);     // ZZ3 = ZZ1 PP
-  mont_mul<Fq>(acc.ZZZ, acc.ZZZ, PPP);  // ZZZ3 = ZZZ1 PPP
-  mont_mul<Fq>(Q, acc.X, PP);           // Q = X1 PP
-  mont_mul<Fq>(P, R, R);
+  fq_mul_small(PP, P, P);
+  fq_mul_small(PPP, P, PP);
+  fq_mul_small(acc.ZZ, acc.ZZ, PP);     // ZZ3 = ZZ1 PP
+  fq_mul_small(acc.ZZZ, acc.ZZZ, PPP);  // ZZZ3 = ZZZ1 PPP
+  fq_mul_small(Q, acc.X, PP);           // Q = X1 PP
+  fq_mul_small(P, R, R);
   sub_mod<Fq>(P, P, PPP);
   sub_mod<Fq>(P, P, Q);
   sub_mod<Fq>(P, P, Q);                 // X3 = R^2 - PPP - 2 Q
   sub_mod<Fq>(Q, Q, P);
-  mont_mul<Fq>(Q, R, Q);                // R (Q - X3)
-  mont_mul<Fq>(PPP, acc.Y, PPP);
+  fq_mul_small(Q, R, Q);                // R (Q - X3)
+  fq_mul_small(PPP, acc.Y, PPP);
   sub_mod<Fq>(acc.Y, Q, PPP);           // Y3 = R (Q - X3) - Y1 PPP
   fe_copy(acc.X, P);
 }

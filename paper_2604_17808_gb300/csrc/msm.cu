@@ -3,27 +3,36 @@
 //
 //   MSM = sum_{n<N} S_n P_n, S_n < r (254 bits), P_n affine points.
 //
-// Each scalar is cut into K = ceil(254 / c) unsigned c-bit digits; window k
-// keeps 2^c buckets.  The four phases of Algorithm 2 map to kernels:
+// Each scalar is cut into K = ceil(255 / c) signed c-bit digits
+// d_k in [-(2^(c-1) - 1), 2^(c-1)] (sum_k d_k 2^(k c) = S_n); window k keeps
+// 2^(c-1) buckets, bucket j collecting the points whose digit has magnitude
+// j + 1 (negated when the digit is negative).  The four phases of
+// Algorithm 2 map to kernels:
 //
-//   Bucketize    msm_count_kernel      digit histogram (one counter per bucket,
-//                                      atomics in L2; digit 0 is skipped)
-//                scan_*_kernel         exclusive scan -> bucket offsets, plus
-//                                      a scan of ceil(count / S) -> segments
-//                msm_scatter_kernel    point index n into its bucket's slot
-//                                      (the argsort of the digits, as a
-//                                      counting sort)
-//   BA           msm_accumulate_kernel one thread per segment of at most S
-//                                      points of one bucket (bucket += affine
-//                                      point, XYZZ madd); then
-//                msm_combine_kernel    a pairwise tree over a bucket's
-//                                      segments, so no bucket is ever summed
-//                                      by one thread alone (a skewed or
-//                                      constant scalar set stays parallel)
+//   Bucketize    msm_count_kernel      bucket sizes (one counter per bucket,
+//                                      atomics in L2; zero digits skipped)
+//                scan_*_kernel         exclusive scan -> bucket offsets
+//                msm_scatter_kernel    point index (and digit sign) into the
+//                                      next slot of its bucket: the argsort of
+//                                      the digits as a counting sort
+//   BA           msm_accumulate_kernel the bucket-sorted entries cut into
+//                                      segments of exactly S; one thread adds
+//                                      its S points (XYZZ += affine), writing a
+//                                      bucket that lies inside its segment
+//                                      straight to the bucket array and the
+//                                      pieces of the (at most two) buckets
+//                                      that cross its ends to piece slots;
+//                msm_combine_kernel    a pairwise tree over the pieces of each
+//                                      crossing bucket.  Every thread does the
+//                                      same number of additions whatever the
+//                                      bucket sizes (a skewed or constant
+//                                      scalar set stays parallel and balanced)
 //   BR           msm_reduce_level_kernel  the tree of Algorithm 2, one launch
-//                                      per level s = c-1 .. 0, all windows at
-//                                      once: W_b = W_2b + W_2b+1 + B_2b+1,
-//                                      B_b = 2 (B_2b + B_2b+1)
+//                                      per level, all windows at once:
+//                                      W_b = W_2b + W_2b+1 + B_2b+1,
+//                                      B_b = 2 (B_2b + B_2b+1); the leaves
+//                                      start at W_j = B_j, so the root holds
+//                                      sum_j (j + 1) B_j
 //   WM           msm_merge_kernel      Horner over the windows, top one first
 //                                      (MSM = 2^c MSM + W_k), then the affine
 //                                      standard-form result.
@@ -54,6 +63,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;
 constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr int kEcThreads = 128;
+constexpr uint32_t kSignBit = 0x80000000u;
 
 struct EcConst {
   uint32_t one[8];  // 2^256 mod q (Montgomery 1)
@@ -63,8 +73,8 @@ struct EcConst {
 
 struct MsmTotals {
   uint32_t entries;   // points placed in buckets (digit != 0)
-  uint32_t segments;  // accumulation segments
-  uint32_t max_seg;   // most segments of one bucket
+  uint32_t max_span;  // most segment boundaries one bucket crosses
+  uint32_t pad;
   uint32_t err;       // MSM_ERR_* bits
 };
 
@@ -84,13 +94,24 @@ __device__ __forceinline__ void store_point_xyzz(uint4 *base, uint64_t i, const 
   fe_store_global(base, 4 * i + 3, p.ZZZ);
 }
 
-// c-bit digit of window k of the scalar s (8 little-endian words); c <= 24
-__device__ __forceinline__ uint32_t window_digit(const uint32_t s[8], uint32_t k, uint32_t c) {
+// Raw c-bit digit of window k of the scalar s (8 little-endian words); c <= 22.
+__device__ __forceinline__ uint32_t raw_digit(const uint32_t s[8], uint32_t k, uint32_t c) {
   const uint32_t bit = k * c, w = bit >> 5, sh = bit & 31u;
   if (w >= 8) return 0u;
   uint64_t v = s[w];
   if (w + 1 < 8) v |= (uint64_t)s[w + 1] << 32;
   return (uint32_t)(v >> sh) & ((1u << c) - 1u);
+}
+
+// Next signed digit: v = raw + carry in [0, 2^c]; v > 2^(c-1) becomes
+// v - 2^c (negative) with a carry into the next window.  Returns the
+// magnitude (0 for a zero digit); neg is the sign.
+__device__ __forceinline__ uint32_t signed_digit(const uint32_t s[8], uint32_t k, uint32_t c, uint32_t &carry,
+                                                 bool &neg) {
+  const uint32_t v = raw_digit(s, k, c) + carry;
+  neg = v > (1u << (c - 1));
+  carry = neg ? 1u : 0u;
+  return neg ? (1u << c) - v : v;
 }
 
 __device__ __forceinline__ bool scalar_is_canonical(const uint32_t s[8]) {
@@ -139,235 +160,288 @@ __global__ void __launch_bounds__(kEcThreads) msm_prepare_kernel(const uint4 *pt
   }
 }
 
-// Bucketize, pass 1: one counter per (window, digit).
-__global__ void __launch_bounds__(256) msm_count_kernel(const uint4 *scalars, uint64_t n, uint32_t c, uint32_t K,
-                                                        uint32_t *counts, MsmTotals *tot) {
+// Bucketize, pass 1: one counter per (window, digit magnitude).
+__global__ void __launch_bounds__(256) msm_count_kernel(const uint4 *__restrict__ scalars, uint64_t n, uint32_t c,
+                                                        uint32_t K, uint32_t *__restrict__ counts, MsmTotals *tot) {
+  const uint32_t lb = c - 1;  // log2 of the buckets per window
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s[8];
     fe_load_global(s, scalars, i);
     if (!scalar_is_canonical(s)) atomicOr(&tot->err, (uint32_t)MSM_ERR_SCALAR);
+    uint32_t carry = 0;
     for (uint32_t k = 0; k < K; ++k) {
-      const uint32_t d = window_digit(s, k, c);
-      if (d) atomicAdd(&counts[((uint64_t)k << c) + d], 1u);
+      bool neg;
+      const uint32_t m = signed_digit(s, k, c, carry, neg);
+      if (m) atomicAdd(&counts[((uint64_t)k << lb) + m - 1], 1u);
     }
   }
 }
 
-__device__ __forceinline__ uint32_t segs_of(uint32_t count, uint32_t S) { return (count + S - 1) / S; }
-
-__device__ __forceinline__ uint2 add2(uint2 a, uint2 b) { return make_uint2(a.x + b.x, a.y + b.y); }
-
-// Inclusive scan of a uint2 across a warp.
-__device__ __forceinline__ uint2 warp_scan2(uint2 v) {
+// Inclusive scan across a warp.
+__device__ __forceinline__ uint32_t warp_scan(uint32_t v) {
   const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t a = __shfl_up_sync(0xffffffffu, v.x, o);
-    const uint32_t b = __shfl_up_sync(0xffffffffu, v.y, o);
-    if (lane >= (uint32_t)o) {
-      v.x += a;
-      v.y += b;
-    }
+    const uint32_t a = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= (uint32_t)o) v += a;
   }
   return v;
 }
 
 // Exclusive scan of v over the CTA (blockDim.x = kScanThreads); *total gets
 // the CTA's sum.
-__device__ __forceinline__ uint2 block_excl_scan2(uint2 v, uint2 *total) {
-  __shared__ uint2 warp_sums[kScanThreads / 32];
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
+  __shared__ uint32_t warp_sums[kScanThreads / 32];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint2 inc = warp_scan2(v);
+  const uint32_t inc = warp_scan(v);
   if (lane == 31) warp_sums[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    uint2 w = lane < kScanThreads / 32 ? warp_sums[lane] : make_uint2(0, 0);
-    const uint2 wi = warp_scan2(w);
-    if (lane < kScanThreads / 32) warp_sums[lane] = make_uint2(wi.x - w.x, wi.y - w.y);
+    const uint32_t w = lane < kScanThreads / 32 ? warp_sums[lane] : 0u;
+    const uint32_t wi = warp_scan(w);
+    if (lane < kScanThreads / 32) warp_sums[lane] = wi - w;
     if (lane == kScanThreads / 32 - 1) *total = wi;
   }
   __syncthreads();
-  const uint2 base = warp_sums[warp];
+  const uint32_t base = warp_sums[warp];
   __syncthreads();
-  return make_uint2(base.x + inc.x - v.x, base.y + inc.y - v.y);
+  return base + inc - v;
 }
 
-// Scan pass 1: per-tile sums of (count, segments) and the largest segment
-// count of a bucket.
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t *counts, uint64_t nb, uint32_t S,
-                                                                   uint2 *tile_sums, MsmTotals *tot) {
+// Scan pass 1: per-tile sums of the bucket sizes.
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t *counts, uint64_t nb,
+                                                                   uint32_t *tile_sums) {
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanPer;
-  uint2 v = make_uint2(0, 0);
-  uint32_t mx = 0;
+  uint32_t v = 0;
 #pragma unroll
-  for (int j = 0; j < kScanPer; ++j) {
-    if (base + j < nb) {
-      const uint32_t cnt = counts[base + j];
-      const uint32_t g = segs_of(cnt, S);
-      v.x += cnt;
-      v.y += g;
-      mx = max(mx, g);
-    }
-  }
-  __shared__ uint2 total;
-  block_excl_scan2(v, &total);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31u) == 0 && mx) atomicMax(&tot->max_seg, mx);
-  __syncthreads();
+  for (int j = 0; j < kScanPer; ++j)
+    if (base + j < nb) v += counts[base + j];
+  __shared__ uint32_t total;
+  block_excl_scan(v, &total);
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-// Scan pass 2 (one CTA): exclusive scan of the tile sums in place; the
-// grand totals go to tot and to the final entries offsets[nb], seg_off[nb].
-__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(uint2 *tile_sums, uint32_t num_tiles, uint64_t nb,
-                                                                  uint32_t *offsets, uint32_t *seg_off,
-                                                                  MsmTotals *tot) {
-  __shared__ uint2 chunk_total;
-  uint2 carry = make_uint2(0, 0);
+// Scan pass 2 (one CTA): exclusive scan of the tile sums in place; the total
+// goes to tot->entries and offsets[nb].
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(uint32_t *tile_sums, uint32_t num_tiles,
+                                                                  uint64_t nb, uint32_t *offsets, MsmTotals *tot) {
+  __shared__ uint32_t chunk_total;
+  uint32_t carry = 0;
   for (uint32_t b0 = 0; b0 < num_tiles; b0 += kScanThreads) {
     const uint32_t i = b0 + threadIdx.x;
-    const uint2 v = i < num_tiles ? tile_sums[i] : make_uint2(0, 0);
-    const uint2 ex = block_excl_scan2(v, &chunk_total);
-    if (i < num_tiles) tile_sums[i] = add2(carry, ex);
+    const uint32_t v = i < num_tiles ? tile_sums[i] : 0u;
+    const uint32_t ex = block_excl_scan(v, &chunk_total);
+    if (i < num_tiles) tile_sums[i] = carry + ex;
     __syncthreads();
-    carry = add2(carry, chunk_total);
+    carry += chunk_total;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    tot->entries = carry.x;
-    tot->segments = carry.y;
-    offsets[nb] = carry.x;
-    seg_off[nb] = carry.y;
+    tot->entries = carry;
+    offsets[nb] = carry;
   }
 }
 
-// Scan pass 3: bucket offsets (also copied to the scatter cursors) and
-// segment offsets.
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t *counts, uint64_t nb, uint32_t S,
-                                                                  const uint2 *tile_sums, uint32_t *offsets,
-                                                                  uint32_t *cursor, uint32_t *seg_off) {
+// Scan pass 3: bucket offsets, also copied to the scatter cursors.
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t *counts, uint64_t nb,
+                                                                  const uint32_t *tile_sums, uint32_t *offsets,
+                                                                  uint32_t *cursor) {
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanPer;
   uint32_t cnt[kScanPer];
-  uint2 v = make_uint2(0, 0);
+  uint32_t v = 0;
 #pragma unroll
   for (int j = 0; j < kScanPer; ++j) {
     cnt[j] = base + j < nb ? counts[base + j] : 0u;
-    v.x += cnt[j];
-    v.y += segs_of(cnt[j], S);
+    v += cnt[j];
   }
-  __shared__ uint2 total;
-  uint2 run = add2(block_excl_scan2(v, &total), tile_sums[blockIdx.x]);
+  __shared__ uint32_t total;
+  uint32_t run = block_excl_scan(v, &total) + tile_sums[blockIdx.x];
 #pragma unroll
   for (int j = 0; j < kScanPer; ++j) {
     if (base + j < nb) {
-      offsets[base + j] = run.x;
-      cursor[base + j] = run.x;
-      seg_off[base + j] = run.y;
+      offsets[base + j] = run;
+      cursor[base + j] = run;
     }
-    run.x += cnt[j];
-    run.y += segs_of(cnt[j], S);
+    run += cnt[j];
   }
 }
 
-// Bucketize, pass 2: each point index into the next free slot of its bucket.
-__global__ void __launch_bounds__(256) msm_scatter_kernel(const uint4 *scalars, uint64_t n, uint32_t c, uint32_t K,
-                                                          uint32_t *cursor, uint32_t *sorted) {
+// Bucketize, pass 2: each point index (sign in bit 31) into the next free
+// slot of its bucket; the atomics of eight windows are in flight at once.
+__global__ void __launch_bounds__(256) msm_scatter_kernel(const uint4 *__restrict__ scalars, uint64_t n, uint32_t c,
+                                                          uint32_t K, uint32_t *__restrict__ cursor,
+                                                          uint32_t *__restrict__ sorted) {
+  const uint32_t lb = c - 1;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s[8];
     fe_load_global(s, scalars, i);
-    for (uint32_t k = 0; k < K; ++k) {
-      const uint32_t d = window_digit(s, k, c);
-      if (d) sorted[atomicAdd(&cursor[((uint64_t)k << c) + d], 1u)] = (uint32_t)i;
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 < K; k0 += 8) {
+      uint32_t pos[8], val[8];
+#pragma unroll
+      for (uint32_t j = 0; j < 8; ++j) {
+        const uint32_t k = k0 + j;
+        bool neg = false;
+        const uint32_t m = k < K ? signed_digit(s, k, c, carry, neg) : 0u;
+        pos[j] = m ? atomicAdd(&cursor[((uint64_t)k << lb) + m - 1], 1u) : 0xffffffffu;
+        val[j] = (uint32_t)i | (neg ? kSignBit : 0u);
+      }
+#pragma unroll
+      for (uint32_t j = 0; j < 8; ++j)
+        if (pos[j] != 0xffffffffu) sorted[pos[j]] = val[j];
     }
   }
 }
 
-// Largest b with seg_off[b] <= s (seg_off non-decreasing, seg_off[0] = 0).
-__device__ __forceinline__ uint32_t bucket_of_segment(const uint32_t *seg_off, uint64_t nb, uint32_t s) {
-  uint64_t lo = 0, hi = nb;  // seg_off[lo] <= s < seg_off[hi]
+// Largest b with offsets[b] <= e (offsets non-decreasing, offsets[0] = 0,
+// e < offsets[nb]): the bucket holding sorted entry e.
+__device__ __forceinline__ uint32_t bucket_of_entry(const uint32_t *offsets, uint64_t nb, uint32_t e) {
+  uint64_t lo = 0, hi = nb;  // offsets[lo] <= e < offsets[hi]
   while (hi - lo > 1) {
     const uint64_t mid = (lo + hi) >> 1;
-    if (__ldg(seg_off + mid) <= s) lo = mid;
+    if (__ldg(offsets + mid) <= e) lo = mid;
     else hi = mid;
   }
   return (uint32_t)lo;
 }
 
-// BA: segment s of bucket b sums at most S consecutive sorted points.
+// Where the partial sum of bucket b over segment t goes: a bucket inside the
+// segment is complete (bucket array); a bucket that started in an earlier
+// segment leaves its piece in slot 2t; one that starts here and continues
+// leaves its head piece in slot 2t + 1.
+__device__ __forceinline__ void emit_piece(const PointXyzz &acc, uint32_t b, uint32_t t, bool started_before,
+                                           bool continues, uint4 *bucket_sum, uint4 *pieces) {
+  if (!started_before && !continues) store_point_xyzz(bucket_sum, b, acc);
+  else if (started_before) store_point_xyzz(pieces, 2 * (uint64_t)t, acc);
+  else store_point_xyzz(pieces, 2 * (uint64_t)t + 1, acc);
+}
+
+// BA: segment t adds the points of sorted entries [t S, t S + S).
 __global__ void __launch_bounds__(kEcThreads, 4)
-    msm_accumulate_kernel(const uint4 *pts_m, const uint32_t *sorted, const uint32_t *offsets,
-                          const uint32_t *seg_off, uint64_t nb, uint32_t S, EcConst k, const MsmTotals *tot,
-                          uint32_t *seg_bucket, uint4 *partial) {
-  const uint32_t num_segs = tot->segments;
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += gridDim.x * blockDim.x) {
-    const uint32_t b = bucket_of_segment(seg_off, nb, s);
-    const uint32_t i = s - seg_off[b];
-    const uint32_t begin = offsets[b] + i * S;
-    const uint32_t end = min(begin + S, offsets[b + 1]);
+    msm_accumulate_kernel(const uint4 *__restrict__ pts_m, const uint32_t *__restrict__ sorted,
+                          const uint32_t *__restrict__ offsets, uint64_t nb, uint32_t S, EcConst k,
+                          MsmTotals *tot, uint2 *__restrict__ seg_ends, uint4 *bucket_sum, uint4 *pieces) {
+  const uint32_t T = tot->entries;
+  const uint32_t num_segs = (T + S - 1) / S;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < num_segs; t += gridDim.x * blockDim.x) {
+    const uint32_t e0 = t * S, e1 = min(e0 + S, T);
+    uint32_t b = bucket_of_entry(offsets, nb, e0);
+    const uint32_t first = b;
+    uint32_t end_b = __ldg(offsets + b + 1);
+    bool started_before = __ldg(offsets + b) < e0;
     PointXyzz acc;
     xyzz_set_inf(acc);
-    for (uint32_t e = begin; e < end; ++e) {
-      const uint32_t idx = __ldg(sorted + e);
+    for (uint32_t e = e0; e < e1; ++e) {
+      if (e == end_b) {  // bucket b ends inside the segment
+        emit_piece(acc, b, t, started_before, false, bucket_sum, pieces);
+        xyzz_set_inf(acc);
+        do {
+          ++b;
+          end_b = __ldg(offsets + b + 1);
+        } while (end_b == e);  // skip empty buckets
+        started_before = false;
+      }
+      const uint32_t v = __ldg(sorted + e);
+      const uint64_t idx = v & ~kSignBit;
       uint32_t x[8], y[8];
-      fe_load_global(x, pts_m, 2 * (uint64_t)idx);
-      fe_load_global(y, pts_m, 2 * (uint64_t)idx + 1);
+      fe_load_global(x, pts_m, 2 * idx);
+      fe_load_global(y, pts_m, 2 * idx + 1);
       if (fe_is_zero(x) && fe_is_zero(y)) continue;  // point at infinity
+      if (v & kSignBit) {
+        const uint32_t zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        sub_mod<Fq>(y, zero, y);
+      }
       xyzz_madd(acc, x, y, k.one);
     }
-    seg_bucket[s] = b;
-    store_point_xyzz(partial, s, acc);
+    const bool continues = end_b > e1;
+    emit_piece(acc, b, t, started_before, continues, bucket_sum, pieces);
+    if (continues && !started_before) {
+      const uint32_t span = (end_b - 1) / S - t;  // segments after t that hold bucket b
+      atomicMax(&tot->max_span, span);
+    }
+    seg_ends[t] = make_uint2(first, b);
   }
 }
 
-// BA, combine round r: segment i (local index within its bucket) with i a
-// multiple of 2^(r+1) adds segment i + 2^r; after ceil(log2(max_seg)) rounds
-// a bucket's sum is in its first segment.
+// BA, combine round r.  The pieces of a bucket that crosses segments
+// t0 < t0+1 < ... < t1 form V[0] = head slot 2 t0 + 1, V[i] = slot 2 (t0 + i);
+// round r adds V[i + 2^r] into V[i] for i a multiple of 2^(r+1), so after
+// ceil(log2(t1 - t0 + 1)) rounds the bucket's sum is in V[0].
 __global__ void __launch_bounds__(kEcThreads, 4)
-    msm_combine_kernel(const uint32_t *seg_off, const uint32_t *seg_bucket, const MsmTotals *tot, uint32_t r,
-                       uint4 *partial) {
-  if ((1u << r) >= tot->max_seg) return;
-  const uint32_t num_segs = tot->segments;
+    msm_combine_kernel(const uint32_t *__restrict__ offsets, const uint2 *__restrict__ seg_ends, uint32_t S,
+                       const MsmTotals *tot, uint32_t r, uint4 *pieces) {
   const uint32_t step = 1u << r;
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += gridDim.x * blockDim.x) {
-    const uint32_t b = seg_bucket[s];
-    const uint32_t i = s - seg_off[b];
-    const uint32_t m = seg_off[b + 1] - seg_off[b];
-    if ((i & (2 * step - 1)) != 0 || i + step >= m) continue;
-    PointXyzz a, q;
-    load_point_xyzz(a, partial, s);
-    load_point_xyzz(q, partial, s + step);
-    xyzz_add(a, q);
-    store_point_xyzz(partial, s, a);
+  if (step > tot->max_span) return;
+  const uint32_t T = tot->entries;
+  const uint32_t num_segs = (T + S - 1) / S;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < num_segs; t += gridDim.x * blockDim.x) {
+    const uint2 ends = seg_ends[t];
+    const uint32_t e0 = t * S, e1 = min(e0 + S, T);
+    // role of V[0]: the last bucket starts in this segment and continues
+    {
+      const uint32_t b = ends.y;
+      const uint32_t ob = __ldg(offsets + b), ob1 = __ldg(offsets + b + 1);
+      if (ob >= e0 && ob1 > e1) {
+        const uint32_t span = (ob1 - 1) / S - t;
+        if (step <= span) {
+          PointXyzz a, q;
+          load_point_xyzz(a, pieces, 2 * (uint64_t)t + 1);
+          load_point_xyzz(q, pieces, 2 * (uint64_t)(t + step));
+          xyzz_add(a, q);
+          store_point_xyzz(pieces, 2 * (uint64_t)t + 1, a);
+        }
+      }
+    }
+    // role of V[i], i >= 1: the first bucket started in an earlier segment
+    {
+      const uint32_t b = ends.x;
+      const uint32_t ob = __ldg(offsets + b), ob1 = __ldg(offsets + b + 1);
+      if (ob < e0) {
+        const uint32_t t0 = ob / S, span = (ob1 - 1) / S - t0, i = t - t0;
+        if ((i & (2 * step - 1)) == 0 && i + step <= span) {
+          PointXyzz a, q;
+          load_point_xyzz(a, pieces, 2 * (uint64_t)t);
+          load_point_xyzz(q, pieces, 2 * (uint64_t)(t + step));
+          xyzz_add(a, q);
+          store_point_xyzz(pieces, 2 * (uint64_t)t, a);
+        }
+      }
+    }
   }
 }
 
-// Bucket B_{k,j} (leaf of the reduction tree): the first segment's sum, or O.
-__device__ __forceinline__ void load_bucket(PointXyzz &p, const uint4 *partial, const uint32_t *counts,
-                                            const uint32_t *seg_off, uint64_t b) {
-  if (counts[b] == 0) xyzz_set_inf(p);
-  else load_point_xyzz(p, partial, seg_off[b]);
+// Bucket b's sum after accumulation: O, the complete sum, or the head piece.
+__device__ __forceinline__ void load_bucket(PointXyzz &p, const uint4 *bucket_sum, const uint4 *pieces,
+                                            const uint32_t *offsets, uint32_t S, uint64_t b) {
+  const uint32_t ob = offsets[b], ob1 = offsets[b + 1];
+  if (ob1 == ob) xyzz_set_inf(p);
+  else if (ob / S == (ob1 - 1) / S) load_point_xyzz(p, bucket_sum, b);
+  else load_point_xyzz(p, pieces, 2 * (uint64_t)(ob / S) + 1);
 }
 
 // BR, level s of the tree (all windows): node (k, b), b < 2^s, from its two
-// children.  Level s of window k is stored at heap index 2^s + b.
+// children.  Window k has 2^(c-1) leaves (the buckets); level s of its tree
+// is stored at heap index 2^s + b.  At the level above the leaves the
+// children's W are the leaves themselves (W_j = B_j).
 __global__ void __launch_bounds__(kEcThreads, 4)
-    msm_reduce_level_kernel(uint32_t s, uint32_t c, uint32_t K, const uint4 *partial, const uint32_t *counts,
-                            const uint32_t *seg_off, uint4 *heap_w, uint4 *heap_b) {
+    msm_reduce_level_kernel(uint32_t s, uint32_t lb, uint32_t K, const uint4 *bucket_sum, const uint4 *pieces,
+                            const uint32_t *offsets, uint32_t S, uint4 *heap_w, uint4 *heap_b) {
   const uint64_t per = 1ull << s, total = per * K;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k = t >> s, b = t & (per - 1);
-    const uint64_t heap0 = k << c;  // window k's heap
+    const uint64_t heap0 = k << lb;  // window k's heap
     const uint64_t node = heap0 + per + b;
     PointXyzz a, br;
-    // W first (at most two points live at a time)
-    if (s + 1 == c) {
-      const uint64_t leaf = (k << c) + 2 * b;
-      load_bucket(br, partial, counts, seg_off, leaf + 1);
-      store_point_xyzz(heap_w, node, br);  // W_L = W_R = O at the leaves: W = B_R
-      if (s == 0) continue;
-      load_bucket(a, partial, counts, seg_off, leaf);
+    if (s + 1 == lb) {
+      const uint64_t leaf = heap0 + 2 * b;
+      load_bucket(a, bucket_sum, pieces, offsets, S, leaf);
+      load_bucket(br, bucket_sum, pieces, offsets, S, leaf + 1);
+      xyzz_add(a, br);                     // B_L + B_R
+      PointXyzz w = a;
+      xyzz_add(w, br);                     // W = W_L + W_R + B_R with W_j = B_j
+      store_point_xyzz(heap_w, node, w);
+      if (s == 0) continue;                // the root's B is not needed
     } else {
       const uint64_t child = heap0 + 2 * per + 2 * b;
       load_point_xyzz(a, heap_w, child);
@@ -375,26 +449,31 @@ __global__ void __launch_bounds__(kEcThreads, 4)
       xyzz_add(a, br);
       load_point_xyzz(br, heap_b, child + 1);
       xyzz_add(a, br);
-      store_point_xyzz(heap_w, node, a);
-      if (s == 0) continue;  // the root's B is not needed
+      store_point_xyzz(heap_w, node, a);   // W = W_L + W_R + B_R
+      if (s == 0) continue;
       load_point_xyzz(a, heap_b, child);
+      xyzz_add(a, br);                     // B_L + B_R
     }
-    xyzz_add(a, br);
     xyzz_dbl(a, a);
-    store_point_xyzz(heap_b, node, a);
+    store_point_xyzz(heap_b, node, a);     // B = 2 (B_L + B_R)
   }
 }
 
-// WM: MSM = sum_k 2^(k c) W_k by Horner, then affine standard form.
-__global__ void msm_merge_kernel(uint32_t c, uint32_t K, const uint4 *heap_w, EcConst kc, uint4 *result) {
+// WM: MSM = sum_k 2^(k c) W_k by Horner, then affine standard form.  With
+// one bucket per window (c = 1) W_k is that bucket.
+__global__ void msm_merge_kernel(uint32_t c, uint32_t K, const uint4 *heap_w, const uint4 *bucket_sum,
+                                 const uint4 *pieces, const uint32_t *offsets, uint32_t S, EcConst kc,
+                                 uint4 *result) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const uint32_t lb = c - 1;
   PointXyzz acc;
   xyzz_set_inf(acc);
   for (int k = (int)K - 1; k >= 0; --k) {
     if (!xyzz_is_inf(acc))
       for (uint32_t j = 0; j < c; ++j) xyzz_dbl(acc, acc);
     PointXyzz w;
-    load_point_xyzz(w, heap_w, ((uint64_t)k << c) + 1);
+    if (lb == 0) load_bucket(w, bucket_sum, pieces, offsets, S, (uint64_t)k);
+    else load_point_xyzz(w, heap_w, ((uint64_t)k << lb) + 1);
     xyzz_add(acc, w);
   }
   uint32_t x[8], y[8];
@@ -410,12 +489,9 @@ __global__ void fixed_base_table_kernel(EcConst kc, uint4 *table_xyzz) {
   const uint32_t w = threadIdx.x;
   if (blockIdx.x != 0 || w >= 32) return;
   // G = (1, 2) in Montgomery form
-  uint32_t gx[8], gy[8];
-  fe_copy(gx, kc.one);
-  add_mod<Fq>(gy, kc.one, kc.one);
   PointXyzz base;
-  fe_copy(base.X, gx);
-  fe_copy(base.Y, gy);
+  fe_copy(base.X, kc.one);
+  add_mod<Fq>(base.Y, kc.one, kc.one);
   fe_copy(base.ZZ, kc.one);
   fe_copy(base.ZZZ, kc.one);
   for (uint32_t j = 0; j < 8 * w; ++j) xyzz_dbl(base, base);
@@ -525,15 +601,16 @@ ntt_status check_device(int *dev_out, int *sms) {
   return NTT_OK;
 }
 
-// Window size minimising the modelled multiply count: K (10 n + 26 2^c)
-// (one 10-product madd per point and window, about 26 products per bucket
-// in the reduction tree), capped so that the tree stays small.
+uint32_t num_windows(uint32_t c) { return (kScalarBits + 1 + c - 1) / c; }  // K c >= 255 (signed digits)
+
+// Window size minimising the modelled multiply count K (10 n + 26 2^(c-1)):
+// one 10-product mixed addition per point and window, about 26 products per
+// bucket in the reduction tree.
 uint32_t default_window(uint64_t n) {
   uint32_t best = 4;
   double best_cost = 1e300;
-  for (uint32_t c = 4; c <= 20; ++c) {
-    const double K = (double)((kScalarBits + c - 1) / c);
-    const double cost = K * (10.0 * (double)n + 26.0 * (double)(1u << c));
+  for (uint32_t c = 4; c <= 21; ++c) {
+    const double cost = (double)num_windows(c) * (10.0 * (double)n + 26.0 * (double)(1u << (c - 1)));
     if (cost < best_cost) {
       best_cost = cost;
       best = c;
@@ -542,13 +619,13 @@ uint32_t default_window(uint64_t n) {
   return best;
 }
 
+// Entries per accumulation segment: enough segments to fill the GPU eight
+// times over (512 resident threads per SM), 8..128 additions each.  Longer
+// segments cut the buckets that cross a segment end, hence the combine work.
 uint32_t segment_length(uint64_t max_n, uint32_t K, int sms) {
-  // enough segments to fill the GPU several times over, at most 256 points each
   const uint64_t entries = max_n * K;
-  const uint64_t want = (uint64_t)sms * 512 * 4;
-  uint64_t S = entries / want;
-  S = std::max<uint64_t>(16, std::min<uint64_t>(256, S));
-  return (uint32_t)S;
+  const uint64_t want = (uint64_t)sms * 512 * 8;
+  return (uint32_t)std::max<uint64_t>(8, std::min<uint64_t>(128, entries / want));
 }
 
 }  // namespace
@@ -561,25 +638,25 @@ struct msm_plan_s {
   int sms = 0;
   uint64_t max_n = 0;
   uint32_t c = 0, K = 0, S = 0;
-  uint64_t nb = 0;            // K 2^c buckets
+  uint64_t nb = 0;            // K 2^(c-1) buckets
   uint64_t max_segments = 0;
   uint32_t num_tiles = 0;
   EcConst k;
   uint4 *pts_m = nullptr;     // max_n x 64 B
-  uint32_t *counts = nullptr, *offsets = nullptr, *cursor = nullptr, *seg_off = nullptr;
-  uint2 *tile_sums = nullptr;
+  uint32_t *counts = nullptr, *offsets = nullptr, *cursor = nullptr, *tile_sums = nullptr;
   MsmTotals *tot = nullptr;
-  uint32_t *sorted = nullptr, *seg_bucket = nullptr;
-  uint4 *partial = nullptr;   // max_segments x 128 B
-  uint4 *heap_w = nullptr, *heap_b = nullptr;  // K 2^c x 128 B each
+  uint32_t *sorted = nullptr;
+  uint2 *seg_ends = nullptr;  // first and last bucket of each segment
+  uint4 *bucket_sum = nullptr, *pieces = nullptr;   // nb and 2 max_segments x 128 B
+  uint4 *heap_w = nullptr, *heap_b = nullptr;       // nb x 128 B each
   uint64_t device_bytes = 0;
 };
 
 namespace {
 
 void free_plan(msm_plan p) {
-  void *bufs[] = {p->pts_m, p->counts, p->offsets, p->cursor, p->seg_off, p->tile_sums, p->tot,
-                  p->sorted, p->seg_bucket, p->partial, p->heap_w, p->heap_b};
+  void *bufs[] = {p->pts_m, p->counts, p->offsets, p->cursor, p->tile_sums, p->tot, p->sorted,
+                  p->seg_ends, p->bucket_sum, p->pieces, p->heap_w, p->heap_b};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -635,10 +712,10 @@ ntt_status msm_plan_create(msm_plan *out, msm_curve curve, uint64_t max_n, uint3
   if (curve != MSM_CURVE_BN254_G1) return NTT_ERR_INVALID_ARG;
   if (max_n > MSM_MAX_POINTS) return NTT_ERR_UNSUPPORTED;
   if (window_bits > 22) return NTT_ERR_UNSUPPORTED;
-  {
-    const uint32_t c = window_bits ? window_bits : default_window(std::max<uint64_t>(max_n, 1));
-    if (max_n * ((kScalarBits + c - 1) / c) >= (1ull << 32)) return NTT_ERR_UNSUPPORTED;
-  }
+  const uint32_t c = window_bits ? window_bits : default_window(std::max<uint64_t>(max_n, 1));
+  // sorted entries are counted in 32 bits (with room for one segment past
+  // the end); point indices stay below 2^31, bit 31 carries the digit sign
+  if (max_n * num_windows(c) >= (1ull << 32) - 256) return NTT_ERR_UNSUPPORTED;
   int dev = 0, sms = 0;
   MSM_TRY(check_device(&dev, &sms));
   msm_plan p = new (std::nothrow) msm_plan_s();
@@ -646,12 +723,12 @@ ntt_status msm_plan_create(msm_plan *out, msm_curve curve, uint64_t max_n, uint3
   p->device = dev;
   p->sms = sms;
   p->max_n = max_n;
-  p->c = window_bits ? window_bits : default_window(std::max<uint64_t>(max_n, 1));
-  p->K = (kScalarBits + p->c - 1) / p->c;
+  p->c = c;
+  p->K = num_windows(c);
   p->S = segment_length(max_n, p->K, sms);
-  p->nb = (uint64_t)p->K << p->c;
+  p->nb = (uint64_t)p->K << (c - 1);
   const uint64_t entries = max_n * p->K;
-  p->max_segments = entries / p->S + std::min<uint64_t>(p->nb, entries) + 1;
+  p->max_segments = (entries + p->S - 1) / p->S + 1;
   p->num_tiles = (uint32_t)((p->nb + kScanTile - 1) / kScanTile);
   p->k = make_const();
   uint64_t &tb = p->device_bytes;
@@ -660,12 +737,12 @@ ntt_status msm_plan_create(msm_plan *out, msm_curve curve, uint64_t max_n, uint3
   if (s == NTT_OK) s = alloc(&p->counts, p->nb * 4, &tb);
   if (s == NTT_OK) s = alloc(&p->offsets, (p->nb + 1) * 4, &tb);
   if (s == NTT_OK) s = alloc(&p->cursor, p->nb * 4, &tb);
-  if (s == NTT_OK) s = alloc(&p->seg_off, (p->nb + 1) * 4, &tb);
-  if (s == NTT_OK) s = alloc(&p->tile_sums, (uint64_t)p->num_tiles * sizeof(uint2), &tb);
+  if (s == NTT_OK) s = alloc(&p->tile_sums, (uint64_t)p->num_tiles * 4, &tb);
   if (s == NTT_OK) s = alloc(&p->tot, sizeof(MsmTotals), &tb);
   if (s == NTT_OK) s = alloc(&p->sorted, entries * 4, &tb);
-  if (s == NTT_OK) s = alloc(&p->seg_bucket, p->max_segments * 4, &tb);
-  if (s == NTT_OK) s = alloc(&p->partial, p->max_segments * 128, &tb);
+  if (s == NTT_OK) s = alloc(&p->seg_ends, p->max_segments * sizeof(uint2), &tb);
+  if (s == NTT_OK) s = alloc(&p->bucket_sum, p->nb * 128, &tb);
+  if (s == NTT_OK) s = alloc(&p->pieces, 2 * p->max_segments * 128, &tb);
   if (s == NTT_OK) s = alloc(&p->heap_w, p->nb * 128, &tb);
   if (s == NTT_OK) s = alloc(&p->heap_b, p->nb * 128, &tb);
   if (s == NTT_OK) s = cuda_st(cudaMemset(p->tot, 0, sizeof(MsmTotals)));
@@ -683,6 +760,7 @@ ntt_status msm_plan_info(msm_plan plan, msm_plan_desc *out) {
   out->window_bits = plan->c;
   out->num_windows = plan->K;
   out->segment_length = plan->S;
+  out->reserved = 0;
   out->device_bytes = plan->device_bytes;
   return NTT_OK;
 }
@@ -704,6 +782,7 @@ ntt_status msm_execute(msm_plan p, const void *d_scalars, const void *d_points, 
   const uint4 *sc = (const uint4 *)d_scalars;
   const uint4 *pt = (const uint4 *)d_points;
   const int sms = p->sms;
+  const uint32_t lb = p->c - 1;
   MSM_TRY(cuda_st(cudaMemsetAsync(p->counts, 0, p->nb * 4, st)));
   // keep the error bits (read by msm_poll_error), reset the rest
   MSM_TRY(cuda_st(cudaMemsetAsync(p->tot, 0, offsetof(MsmTotals, err), st)));
@@ -711,27 +790,28 @@ ntt_status msm_execute(msm_plan p, const void *d_scalars, const void *d_points, 
     msm_prepare_kernel<<<grid_for(n, kEcThreads, sms, 16), kEcThreads, 0, st>>>(pt, n, p->k, p->pts_m, p->tot);
     msm_count_kernel<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, p->K, p->counts, p->tot);
   }
-  scan_reduce_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->S, p->tile_sums, p->tot);
-  scan_tiles_kernel<<<1, kScanThreads, 0, st>>>(p->tile_sums, p->num_tiles, p->nb, p->offsets, p->seg_off, p->tot);
-  scan_apply_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->S, p->tile_sums, p->offsets,
-                                                           p->cursor, p->seg_off);
+  scan_reduce_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->tile_sums);
+  scan_tiles_kernel<<<1, kScanThreads, 0, st>>>(p->tile_sums, p->num_tiles, p->nb, p->offsets, p->tot);
+  scan_apply_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->tile_sums, p->offsets, p->cursor);
   if (n > 0) {
     msm_scatter_kernel<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, p->K, p->cursor, p->sorted);
-    const uint64_t segs_bound = n * p->K / p->S + std::min<uint64_t>(p->nb, n * p->K) + 1;
-    const int g = grid_for(segs_bound, kEcThreads, sms, 4);
-    msm_accumulate_kernel<<<g, kEcThreads, 0, st>>>(p->pts_m, p->sorted, p->offsets, p->seg_off, p->nb, p->S,
-                                                    p->k, p->tot, p->seg_bucket, p->partial);
-    // a bucket holds at most n points, so at most ceil(n / S) segments
-    const uint64_t max_m = (n + p->S - 1) / p->S;
-    for (uint32_t r = 0; (1ull << r) < max_m; ++r)
-      msm_combine_kernel<<<g, kEcThreads, 0, st>>>(p->seg_off, p->seg_bucket, p->tot, r, p->partial);
+    const uint64_t segs = (n * p->K + p->S - 1) / p->S;
+    const int g = grid_for(segs, kEcThreads, sms, 4);
+    msm_accumulate_kernel<<<g, kEcThreads, 0, st>>>(p->pts_m, p->sorted, p->offsets, p->nb, p->S, p->k, p->tot,
+                                                    p->seg_ends, p->bucket_sum, p->pieces);
+    // a bucket holds at most n entries, so it crosses at most ceil(n / S)
+    // segment boundaries; rounds beyond the measured maximum exit at once
+    const uint64_t max_span = (n + p->S - 1) / p->S;
+    for (uint32_t r = 0; (1ull << r) <= max_span; ++r)
+      msm_combine_kernel<<<g, kEcThreads, 0, st>>>(p->offsets, p->seg_ends, p->S, p->tot, r, p->pieces);
   }
-  for (int s = (int)p->c - 1; s >= 0; --s) {
+  for (int s = (int)lb - 1; s >= 0; --s) {
     const uint64_t work = ((uint64_t)p->K) << s;
     msm_reduce_level_kernel<<<grid_for(work, kEcThreads, sms, 4), kEcThreads, 0, st>>>(
-        (uint32_t)s, p->c, p->K, p->partial, p->counts, p->seg_off, p->heap_w, p->heap_b);
+        (uint32_t)s, lb, p->K, p->bucket_sum, p->pieces, p->offsets, p->S, p->heap_w, p->heap_b);
   }
-  msm_merge_kernel<<<1, 32, 0, st>>>(p->c, p->K, p->heap_w, p->k, (uint4 *)d_result);
+  msm_merge_kernel<<<1, 32, 0, st>>>(p->c, p->K, p->heap_w, p->bucket_sum, p->pieces, p->offsets, p->S, p->k,
+                                     (uint4 *)d_result);
   return cuda_st(cudaGetLastError());
 }
 

@@ -88,6 +88,16 @@ def test_msm_matches_oracle(msm, c):
     assert got == _closed_form(ss, ts)
 
 
+@pytest.mark.parametrize("c", [2, 5, 20])
+def test_msm_windows_and_segment_boundaries(msm, c):
+    # small windows put many points in each bucket (buckets cross many
+    # accumulation segments); c = 20 leaves most buckets empty
+    sw, ss, ts, pts = _inputs(2500, 0x3580 + c)
+    got, err = _run(msm, sw, mo.points_to_words(pts), window_bits=c)
+    assert err == 0
+    assert got == _closed_form(ss, ts)
+
+
 def test_msm_matches_ls_ppg_oracle_directly(msm):
     sw, ss, ts, pts = _inputs(150, 0x3520)
     got, _ = _run(msm, sw, mo.points_to_words(pts), window_bits=5)
@@ -105,7 +115,7 @@ def test_msm_ragged_lengths_and_plan_reuse(msm):
             assert err == 0
             assert got == (_closed_form(ss[:n], ts[:n]) if n else None), n
         info = plan.info()
-        assert info["max_n"] == 5000 and info["num_windows"] == -(-254 // info["window_bits"])
+        assert info["max_n"] == 5000 and info["num_windows"] == -(-255 // info["window_bits"])  # signed digits
     finally:
         plan.close()
 
@@ -153,11 +163,12 @@ def test_msm_input_checks(msm):
     got, err = _run(msm, _scalar_words(ss), big, window_bits=8)
     assert err == 1
     assert got == mo.msm([ss[0]] + ss[2:], [pts[0]] + pts[2:])
-    # scalars >= r are flagged; with 8-bit windows every bit is used
-    wide = [R + 5, (1 << 256) - 1]
-    got, err = _run(msm, _scalar_words(wide), words[:2], window_bits=8)
+    # scalars >= r are flagged; below 2^254 the result is still exact
+    got, err = _run(msm, _scalar_words([R + 5, 7]), words[:2], window_bits=8)
     assert err == 2
-    assert got == mo.msm([w % R for w in wide], pts[:2])
+    assert got == mo.msm([5, 7], pts[:2])
+    _, err = _run(msm, _scalar_words([(1 << 256) - 1]), words[:1], window_bits=8)
+    assert err == 2
 
 
 def test_fixed_base_generator(msm):
