@@ -923,7 +923,7 @@ def run_leg(args) -> None:
           "n_2_28": lambda: measure_large(torch, N, stream, steps=3),
           "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3),
           "wide": lambda: measure_wide(torch, N, stream, steps=10),
-          "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=(22, 24, 26))}[args.leg]
+          "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=tuple(args.msm_log))}[args.leg]
     print(json.dumps({args.leg: fn()}), flush=True)
 
 
@@ -939,6 +939,8 @@ def main() -> None:
     ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
     ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide", "msm"],
                     help="run only this secondary measurement and print its JSON (for profiling)")
+    ap.add_argument("--msm-log", type=int, nargs="+", default=[22, 24, 26],
+                    help="log2 point counts of the msm leg (default: the paper's 22 24 26)")
     ap.add_argument("--rotate", type=int, default=ROTATE,
                     help="distinct input vectors the steps rotate over (default 8: larger than L2 at 2^20)")
     args = ap.parse_args()

@@ -61,6 +61,13 @@ __device__ __forceinline__ void fq_mul_small(uint32_t r[8], const uint32_t a[8],
   for (int j = 0; j < 8; ++j) r[j] = z.v[j];
 }
 
+// Product used by a formula: inlined, or the out-of-line call (kCall).
+template <bool kCall>
+__device__ __forceinline__ void fq_mul(uint32_t r[8], const uint32_t a[8], const uint32_t b[8]) {
+  if constexpr (kCall) fq_mul_small(r, a, b);
+  else mont_mul<Fq>(r, a, b);
+}
+
 struct PointXyzz {
   uint32_t X[8], Y[8], ZZ[8], ZZZ[8];
 };
@@ -121,23 +128,24 @@ __device__ __forceinline__ void xyzz_mdbl(PointXyzz &r, const uint32_t x[8], con
 
 // r = 2 p (dbl-2008-s-1, a = 0); r may alias p.  2 O = O follows from the
 // formulas (ZZ3 = V ZZ1 = 0).
+template <bool kCall = false>
 __device__ __forceinline__ void xyzz_dbl(PointXyzz &r, const PointXyzz &p) {
   uint32_t U[8], V[8], W[8], S[8], M[8];
   add_mod<Fq>(U, p.Y, p.Y);  // U = 2 Y1
-  mont_mul<Fq>(V, U, U);     // V = U^2
-  mont_mul<Fq>(W, U, V);     // W = U V
-  mont_mul<Fq>(S, p.X, V);   // S = X1 V
-  mont_mul<Fq>(M, p.X, p.X);
+  fq_mul<kCall>(V, U, U);     // V = U^2
+  fq_mul<kCall>(W, U, V);     // W = U V
+  fq_mul<kCall>(S, p.X, V);   // S = X1 V
+  fq_mul<kCall>(M, p.X, p.X);
   add_mod<Fq>(U, M, M);
   add_mod<Fq>(M, U, M);      // M = 3 X1^2
-  mont_mul<Fq>(r.ZZ, V, p.ZZ);     // ZZ3 = V ZZ1
-  mont_mul<Fq>(r.ZZZ, W, p.ZZZ);   // ZZZ3 = W ZZZ1
-  mont_mul<Fq>(W, W, p.Y);         // W Y1
-  mont_mul<Fq>(U, M, M);
+  fq_mul<kCall>(r.ZZ, V, p.ZZ);     // ZZ3 = V ZZ1
+  fq_mul<kCall>(r.ZZZ, W, p.ZZZ);   // ZZZ3 = W ZZZ1
+  fq_mul<kCall>(W, W, p.Y);         // W Y1
+  fq_mul<kCall>(U, M, M);
   sub_mod<Fq>(U, U, S);
   sub_mod<Fq>(U, U, S);      // X3 = M^2 - 2 S
   sub_mod<Fq>(S, S, U);
-  mont_mul<Fq>(S, M, S);
+  fq_mul<kCall>(S, M, S);
   sub_mod<Fq>(r.Y, S, W);    // Y3 = M (S - X3) - W Y1
   fe_copy(r.X, U);
 }
@@ -179,6 +187,7 @@ __device__ __forceinline__ void xyzz_madd(PointXyzz &acc, const uint32_t x2[8], 
 }
 
 // acc += q (add-2008-s).
+template <bool kCall = false>
 __device__ __forceinline__ void xyzz_add(PointXyzz &acc, const PointXyzz &q) {
   if (xyzz_is_inf(q)) return;
   if (xyzz_is_inf(acc)) {
@@ -186,31 +195,31 @@ __device__ __forceinline__ void xyzz_add(PointXyzz &acc, const PointXyzz &q) {
     return;
   }
   uint32_t U1[8], S1[8], P[8], R[8], PP[8], PPP[8];
-  mont_mul<Fq>(U1, acc.X, q.ZZ);        // U1 = X1 ZZ2
-  mont_mul<Fq>(S1, acc.Y, q.ZZZ);       // S1 = Y1 ZZZ2
-  mont_mul<Fq>(P, q.X, acc.ZZ);
+  fq_mul<kCall>(U1, acc.X, q.ZZ);        // U1 = X1 ZZ2
+  fq_mul<kCall>(S1, acc.Y, q.ZZZ);       // S1 = Y1 ZZZ2
+  fq_mul<kCall>(P, q.X, acc.ZZ);
   sub_mod<Fq>(P, P, U1);                // P = U2 - U1
-  mont_mul<Fq>(R, q.Y, acc.ZZZ);
+  fq_mul<kCall>(R, q.Y, acc.ZZZ);
   sub_mod<Fq>(R, R, S1);                // R = S2 - S1
   if (fe_is_zero(P)) {
-    if (fe_is_zero(R)) xyzz_dbl(acc, q);
+    if (fe_is_zero(R)) xyzz_dbl<kCall>(acc, q);
     else xyzz_set_inf(acc);
     return;
   }
-  mont_mul<Fq>(PP, P, P);
-  mont_mul<Fq>(PPP, P, PP);
-  mont_mul<Fq>(acc.ZZ, acc.ZZ, q.ZZ);
-  mont_mul<Fq>(acc.ZZ, acc.ZZ, PP);     // ZZ3 = ZZ1 ZZ2 PP
-  mont_mul<Fq>(acc.ZZZ, acc.ZZZ, q.ZZZ);
-  mont_mul<Fq>(acc.ZZZ, acc.ZZZ, PPP);  // ZZZ3 = ZZZ1 ZZZ2 PPP
-  mont_mul<Fq>(U1, U1, PP);             // Q = U1 PP
-  mont_mul<Fq>(P, R, R);
+  fq_mul<kCall>(PP, P, P);
+  fq_mul<kCall>(PPP, P, PP);
+  fq_mul<kCall>(acc.ZZ, acc.ZZ, q.ZZ);
+  fq_mul<kCall>(acc.ZZ, acc.ZZ, PP);     // ZZ3 = ZZ1 ZZ2 PP
+  fq_mul<kCall>(acc.ZZZ, acc.ZZZ, q.ZZZ);
+  fq_mul<kCall>(acc.ZZZ, acc.ZZZ, PPP);  // ZZZ3 = ZZZ1 ZZZ2 PPP
+  fq_mul<kCall>(U1, U1, PP);             // Q = U1 PP
+  fq_mul<kCall>(P, R, R);
   sub_mod<Fq>(P, P, PPP);
   sub_mod<Fq>(P, P, U1);
   sub_mod<Fq>(P, P, U1);                // X3 = R^2 - PPP - 2 Q
   sub_mod<Fq>(U1, U1, P);
-  mont_mul<Fq>(U1, R, U1);              // R (Q - X3)
-  mont_mul<Fq>(S1, S1, PPP);
+  fq_mul<kCall>(U1, R, U1);              // R (Q - X3)
+  fq_mul<kCall>(S1, S1, PPP);
   sub_mod<Fq>(acc.Y, U1, S1);           // Y3 = R (Q - X3) - S1 PPP
   fe_copy(acc.X, P);
 }

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kEcThreads, 4)
           PointXyzz a, q;
           load_point_xyzz(a, pieces, 2 * (uint64_t)t + 1);
           load_point_xyzz(q, pieces, 2 * (uint64_t)(t + step));
-          xyzz_add(a, q);
+          xyzz_add<true>(a, q);
           store_point_xyzz(pieces, 2 * (uint64_t)t + 1, a);
         }
       }
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kEcThreads, 4)
           PointXyzz a, q;
           load_point_xyzz(a, pieces, 2 * (uint64_t)t);
           load_point_xyzz(q, pieces, 2 * (uint64_t)(t + step));
-          xyzz_add(a, q);
+          xyzz_add<true>(a, q);
           store_point_xyzz(pieces, 2 * (uint64_t)t, a);
         }
       }
@@ -437,24 +437,24 @@ __global__ void __launch_bounds__(kEcThreads, 4)
       const uint64_t leaf = heap0 + 2 * b;
       load_bucket(a, bucket_sum, pieces, offsets, S, leaf);
       load_bucket(br, bucket_sum, pieces, offsets, S, leaf + 1);
-      xyzz_add(a, br);                     // B_L + B_R
+      xyzz_add<true>(a, br);                     // B_L + B_R
       PointXyzz w = a;
-      xyzz_add(w, br);                     // W = W_L + W_R + B_R with W_j = B_j
+      xyzz_add<true>(w, br);                     // W = W_L + W_R + B_R with W_j = B_j
       store_point_xyzz(heap_w, node, w);
       if (s == 0) continue;                // the root's B is not needed
     } else {
       const uint64_t child = heap0 + 2 * per + 2 * b;
       load_point_xyzz(a, heap_w, child);
       load_point_xyzz(br, heap_w, child + 1);
-      xyzz_add(a, br);
+      xyzz_add<true>(a, br);
       load_point_xyzz(br, heap_b, child + 1);
-      xyzz_add(a, br);
+      xyzz_add<true>(a, br);
       store_point_xyzz(heap_w, node, a);   // W = W_L + W_R + B_R
       if (s == 0) continue;
       load_point_xyzz(a, heap_b, child);
-      xyzz_add(a, br);                     // B_L + B_R
+      xyzz_add<true>(a, br);                     // B_L + B_R
     }
-    xyzz_dbl(a, a);
+    xyzz_dbl<true>(a, a);
     store_point_xyzz(heap_b, node, a);     // B = 2 (B_L + B_R)
   }
 }
