@@ -138,14 +138,16 @@ def test_msm_degenerate_inputs(msm):
         assert got == mo.msm(scal, points), name
 
 
-def test_msm_constant_scalars_spread_over_segments(msm):
+@pytest.mark.parametrize("c", [8, 16])
+def test_msm_constant_scalars_spread_over_segments(msm, c):
     # every point in the same bucket of every window: the bucket is summed by
-    # many segments and the pairwise combine tree
+    # many segments and the pairwise combine tree (c = 16 sorts through the
+    # two-level bucketize, c = 8 through the one-level one)
     n = 3000
     ts = limbs_to_ints(ntt_synth.uniform_elements("bn254_fr", n, 0x3550))
     pts = mo.fixed_base_points(ts)
     s = 0x1234_5678_9ABC_DEF0_0FED_CBA9_8765_4321
-    got, err = _run(msm, _scalar_words([s] * n), mo.points_to_words(pts), window_bits=8)
+    got, err = _run(msm, _scalar_words([s] * n), mo.points_to_words(pts), window_bits=c)
     assert err == 0
     assert got == mo.scalar_mul(CURVE, s * (sum(ts) % R) % R, G)
 
