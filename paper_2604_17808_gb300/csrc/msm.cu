@@ -817,6 +817,8 @@ ntt_status msm_execute(msm_plan p, const void *d_scalars, const void *d_points, 
 
 ntt_status msm_poll_error(msm_plan p, uint32_t *flags) {
   if (!p || !flags) return NTT_ERR_INVALID_ARG;
+  // the calls may run on non-blocking streams: wait for all of them
+  MSM_TRY(cuda_st(cudaDeviceSynchronize()));
   MsmTotals t;
   MSM_TRY(cuda_st(cudaMemcpy(&t, p->tot, sizeof(t), cudaMemcpyDeviceToHost)));
   *flags = t.err;
