@@ -245,3 +245,41 @@ def test_mutant_msm_and_ppg_are_caught(monkeypatch):
     assert mo.msm_ls_ppg(ss, pts, 4) != closed
     monkeypatch.undo()
     assert mo.msm_ls_ppg(ss, pts, 4) == closed
+
+
+# ------------------------------------------------------------ BLS12-381 G1
+
+def test_bls12_381_generator_and_order():
+    c = mo.BLS12_381_G1
+    G = mo.BLS12_381_G
+    assert c.on_curve(G)
+    assert mo.scalar_mul(c, mo.BLS12_381_R, G) is None  # G has order r (r prime, G != O)
+    assert mo.scalar_mul(c, mo.BLS12_381_R - 1, G) == c.neg(G)
+    assert mo.BLS12_381_Q.bit_length() == 381 and mo.BLS12_381_Q % 4 == 3
+    # the subgroup order is the scalar field of the transforms
+    assert mo.BLS12_381_R == ntt_synth.MODULI["bls12_381_fr"]
+
+
+def test_bls12_381_msm_closed_form_and_ls_ppg():
+    c = mo.BLS12_381_G1
+    n = 12
+    ts = [int(v) for v in _ints(ntt_synth.uniform_elements("bls12_381_fr", n, 81))]
+    ss = [int(v) for v in _ints(ntt_synth.uniform_elements("bls12_381_fr", n, 82))]
+    pts = mo.fixed_base_points(ts, c)
+    for t, P in zip(ts[:3], pts[:3]):
+        assert P == mo.scalar_mul(c, t, mo.BLS12_381_G)
+    expect = mo.scalar_mul(c, sum(s * t for s, t in zip(ss, ts)) % mo.BLS12_381_R, mo.BLS12_381_G)
+    assert mo.msm(ss, pts, c) == expect
+    for w in (3, 8):
+        assert mo.msm_ls_ppg(ss, pts, w, c, mo.BLS12_381_SCALAR_BITS) == expect
+    # top scalar bit 254 set: the 255-bit windows must cover it
+    big = [(1 << 254) + 3, mo.BLS12_381_R - 1]
+    assert mo.msm_ls_ppg(big, pts[:2], 8, c, 255) == mo.msm(big, pts[:2], c)
+
+
+def test_point_words_round_trip():
+    c = mo.BLS12_381_G1
+    pts = [mo.BLS12_381_G, None, c.double(mo.BLS12_381_G)]
+    w = mo.points_to_words(pts, limbs=6)
+    assert w.shape == (3, 12)
+    assert mo.words_to_points(w, limbs=6) == pts
