@@ -363,30 +363,36 @@ PAPER_MSM_MS = {22: 1.61, 24: 6.42, 26: 25.64}
 MSM_CONFIG = 6  # seeds of the MSM inputs (shared with the tests)
 
 
-def msm_inputs(torch, N, stream, n: int):
+# curve -> (scalar field, seed configuration of its inputs)
+MSM_CURVES = {"bn254_g1": ("bn254_fr", MSM_CONFIG), "bls12_381_g1": ("bls12_381_fr", MSM_CONFIG + 1)}
+
+
+def msm_inputs(torch, N, stream, n: int, curve: str = "bn254_g1"):
     """Scalars uniform in [0, r); points t_n G from the library's fixed-base
     generator (t_n seeded uniform), so that the result has a closed form."""
-    d_s = to_dev(torch, uniform_elements("bn254_fr", n, config_seed(MSM_CONFIG)))
-    d_t = to_dev(torch, uniform_elements("bn254_fr", n, config_seed(MSM_CONFIG, 1)))
-    pts = torch.empty((n, 8), dtype=torch.int64, device=d_s.device)
-    N.msm_fixed_base("bn254_g1", d_t, n, pts, stream)
+    field, cfg = MSM_CURVES[curve]
+    d_s = to_dev(torch, uniform_elements(field, n, config_seed(cfg)))
+    d_t = to_dev(torch, uniform_elements(field, n, config_seed(cfg, 1)))
+    pts = torch.empty((n, N.msm_point_bytes(curve) // 8), dtype=torch.int64, device=d_s.device)
+    N.msm_fixed_base(curve, d_t, n, pts, stream)
     torch.cuda.synchronize()
     del d_t
     return d_s, pts
 
 
-def measure_msm(torch, N, stream, reps: int, log_sizes=(22, 24)) -> dict:
-    """Multi-scalar multiplication on BN254 G1 (Algorithm 2, LS-PPG): the
-    whole call (point conversion, bucketize, accumulation, tree reduction,
-    window merge) timed with CUDA events; the paper's sizes 2^22..2^26."""
+def measure_msm(torch, N, stream, reps: int, log_sizes=(22, 24), curve: str = "bn254_g1") -> dict:
+    """Multi-scalar multiplication on BN254 G1 or BLS12-381 G1 (Algorithm 2,
+    LS-PPG): the whole call (point conversion, bucketize, accumulation, tree
+    reduction, window merge) timed with CUDA events; the paper's sizes
+    2^22..2^26."""
     out = {}
     peak = imad_peak_tops()
     for lg in log_sizes:
         n = 1 << lg
-        d_s, pts = msm_inputs(torch, N, stream, n)
-        plan = N.msm_plan_create("bn254_g1", n, 0)
+        d_s, pts = msm_inputs(torch, N, stream, n, curve)
+        plan = N.msm_plan_create(curve, n, 0)
         info = N.msm_plan_info(plan)
-        res = torch.empty(8, dtype=torch.int64, device=d_s.device)
+        res = torch.empty(pts.shape[1], dtype=torch.int64, device=d_s.device)
         N.msm_execute(plan, d_s, pts, n, res, stream)
         torch.cuda.synchronize()
         first = res.clone()
@@ -402,18 +408,22 @@ def measure_msm(torch, N, stream, reps: int, log_sizes=(22, 24)) -> dict:
         ms = float(np.median(times))
         c, K = info["window_bits"], info["num_windows"]
         # algorithmic products: one 10-product mixed addition per point and
-        # window, about 26 per bucket (2^(c-1) per window) in the reduction tree
+        # window, about 26 per bucket (2^(c-1) per window) in the reduction tree;
+        # a product of D 32-bit limbs is 2 (2 D^2 + D) IMAD (272 for D = 8)
         modmuls = K * n * 10 + K * (1 << (c - 1)) * 26
-        achieved = modmuls * IMAD_PER_MODMUL / (ms * 1e-3) / 1e12
+        limbs = pts.shape[1]  # 32-bit limbs per coordinate = 64-bit words per point
+        imad_per = 2 * (2 * limbs * limbs + limbs)
+        achieved = modmuls * imad_per / (ms * 1e-3) / 1e12
         out[f"n_2_{lg}"] = {"ms": round(ms, 3), "points_per_s": n / (ms * 1e-3), "window_bits": c, "windows": K,
                             "segment_length": info["segment_length"], "plan_device_gb":
                             round(info["device_bytes"] / 1e9, 2), "algorithmic_modmuls": modmuls,
                             "imad_frac": round(achieved / peak, 4), "repeatable": bool(torch.equal(res, first)),
-                            "device_error": N.msm_poll_error(plan), "paper_tpu_ms": PAPER_MSM_MS.get(lg)}
+                            "device_error": N.msm_poll_error(plan),
+                            "paper_tpu_ms": PAPER_MSM_MS.get(lg) if curve == "bn254_g1" else None}
         N.msm_plan_destroy(plan)
         del d_s, pts
         torch.cuda.empty_cache()
-    out["workload"] = ("MSM on BN254 G1 by Layout-Stationary Pippenger, scalars uniform < r, points t_n G "
+    out["workload"] = (f"MSM on {curve} by Layout-Stationary Pippenger, scalars uniform < r, points t_n G "
                        "(seeded), result checked against the closed form in the tests")
     return out
 
@@ -799,6 +809,7 @@ def run_ours(args) -> None:
                          "modmul": measure_modmul(torch, N, stream),
                          "quotient_step": measure_quotient(torch, N, stream, reps=5),
                          "msm_bn254": measure_msm(torch, N, stream, reps=3),
+                         "msm_bls12_381": measure_msm(torch, N, stream, reps=3, curve="bls12_381_g1"),
                          "serving": measure_serving(torch, N, rates=(100, 1000, 5000), seconds=0.5, min_jobs=40)}
         if world == 1 and not args.no_cpu:
             cpu = cpu_baseline(host_inputs[0])
@@ -923,7 +934,8 @@ def run_leg(args) -> None:
           "n_2_28": lambda: measure_large(torch, N, stream, steps=3),
           "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3),
           "wide": lambda: measure_wide(torch, N, stream, steps=10),
-          "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=tuple(args.msm_log))}[args.leg]
+          "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=tuple(args.msm_log), curve=args.msm_curve)
+          }[args.leg]
     print(json.dumps({args.leg: fn()}), flush=True)
 
 
@@ -941,6 +953,8 @@ def main() -> None:
                     help="run only this secondary measurement and print its JSON (for profiling)")
     ap.add_argument("--msm-log", type=int, nargs="+", default=[22, 24, 26],
                     help="log2 point counts of the msm leg (default: the paper's 22 24 26)")
+    ap.add_argument("--msm-curve", choices=["bn254_g1", "bls12_381_g1"], default="bn254_g1",
+                    help="curve of the msm leg")
     ap.add_argument("--rotate", type=int, default=ROTATE,
                     help="distinct input vectors the steps rotate over (default 8: larger than L2 at 2^20)")
     args = ap.parse_args()

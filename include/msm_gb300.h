@@ -10,17 +10,29 @@
  *
  * The result is a group element, so it is exact and unique.
  *
- * Curve: BN254 G1, y^2 = x^3 + 3 over F_q,
- *   q = 0x30644e72e131a029b85045b68181585d97816a916871ca8d3c208c16d87cfd47,
- * a group of prime order r = the BN254 scalar-field modulus (ntt_gb300.h's
- * NTT_FIELD_BN254_FR), generator G = (1, 2).
+ * Curves:
+ *   MSM_CURVE_BN254_G1      y^2 = x^3 + 3 over F_q,
+ *     q = 0x30644e72e131a029b85045b68181585d97816a916871ca8d3c208c16d87cfd47,
+ *     prime order r = the BN254 scalar field (ntt_gb300.h's NTT_FIELD_BN254_FR),
+ *     generator (1, 2);
+ *   MSM_CURVE_BLS12_381_G1  y^2 = x^3 + 4 over the 381-bit F_q,
+ *     q = 0x1a0111ea397fe69a4b1ba7b6434bacd764774b84f38512bf6730d2a0f6b0f6241eabfffeb153ffffb9feffffffffaaab,
+ *     points of the subgroup of prime order r = the BLS12-381 scalar field
+ *     (NTT_FIELD_BLS12_381_FR), its standard generator.
  *
- * Data layout (device buffers, 32-byte aligned):
- *   scalars  N x 32 bytes: four little-endian uint64 limbs, canonical in [0, r);
- *   points   N x 64 bytes: affine x then y, each four little-endian uint64
- *            limbs, standard (not Montgomery) form, canonical in [0, q); the
- *            point at infinity is encoded as x = y = 0 (not a curve point);
- *   result   64 bytes, same encoding as one point.
+ * Data layout (device buffers):
+ *   scalars  N x 32 bytes: four little-endian uint64 limbs, canonical in [0, r),
+ *            32-byte aligned;
+ *   points   N x (2 E) bytes, E = 32 (BN254) or 48 (BLS12-381) = msm_point_bytes / 2:
+ *            affine x then y, each E / 8 little-endian uint64 limbs, standard
+ *            (not Montgomery) form, canonical in [0, q); the point at
+ *            infinity is encoded as x = y = 0 (not a curve point); aligned
+ *            to 32 bytes (BN254) or 16 bytes (BLS12-381);
+ *   result   one point, same encoding and alignment.
+ *
+ * Points are taken to lie in the prime-order group: BN254 G1 is the whole
+ * curve; on BLS12-381 the caller supplies subgroup points (a point on the
+ * curve but outside the subgroup is not detected).
  *
  * Ownership: the caller owns scalars, points and result.  A plan owns its
  * device scratch (a Montgomery copy of the points, the bucket index arrays,
@@ -53,7 +65,8 @@ extern "C" {
 #endif
 
 typedef enum msm_curve {
-    MSM_CURVE_BN254_G1 = 0
+    MSM_CURVE_BN254_G1 = 0,
+    MSM_CURVE_BLS12_381_G1 = 1
 } msm_curve;
 
 #define MSM_MAX_POINTS (1ull << 28)
@@ -65,11 +78,14 @@ typedef struct msm_plan_s *msm_plan;
 typedef struct msm_plan_desc {
     uint64_t max_n;          /* largest n accepted by msm_execute */
     uint32_t window_bits;    /* c: signed digits of c bits, 2^(c-1) buckets per window */
-    uint32_t num_windows;    /* K = ceil(255 / c) */
+    uint32_t num_windows;    /* K = ceil((S + 1) / c), S = 254 (BN254) or 255 (BLS12-381) scalar bits */
     uint32_t segment_length; /* points summed by one thread before the tree */
     uint32_t reserved;
     uint64_t device_bytes;   /* scratch owned by the plan */
 } msm_plan_desc;
+
+/* Bytes of one affine point of `curve` (64 or 96). */
+ntt_status msm_point_bytes(msm_curve curve, uint32_t *bytes);
 
 /* Plan for up to max_n points.  window_bits = 0 picks c from max_n; for
  * window_bits = 1 every window holds one bucket. */
@@ -85,8 +101,8 @@ ntt_status msm_poll_error(msm_plan plan, uint32_t *flags);
 
 /* Fixed-base generation of inputs: points[n] = scalars[n] G (affine, standard
  * form; a zero scalar gives the point at infinity), any scalars < 2^256.
- * The first call on a device builds and keeps a 512 KiB comb table of
- * multiples of G (it synchronises `stream` once). */
+ * The first call per device and curve builds and keeps a comb table of 8192
+ * multiples of G (512 or 768 KiB; it synchronises `stream` once). */
 ntt_status msm_fixed_base(msm_curve curve, const void *d_scalars, uint64_t count, void *d_points,
                           ntt_stream stream);
 

@@ -7,7 +7,7 @@ include/ntt_gb300.h); this package is its thin Python binding:
   * ``_build``   -- the nvcc build of the library;
   * ``Plan``     -- a small owner object over a plan handle for torch users;
   * ``MsmPlan``  -- the same for the multi-scalar multiplication on BN254 G1
-                    (C ABI in include/msm_gb300.h).
+                    or BLS12-381 G1 (C ABI in include/msm_gb300.h).
 
 Importing the package does not load CUDA; the first call does, and raises if
 the library has not been built.
@@ -25,6 +25,7 @@ from ._native import (  # noqa: F401
     msm_execute,
     msm_fixed_base,
     msm_plan_create,
+    msm_point_bytes,
     msm_plan_destroy,
     msm_plan_info,
     msm_poll_error,
@@ -100,13 +101,15 @@ class Plan:
 
 
 class MsmPlan:
-    """Owns one msm_plan handle.  Scalars: torch int64 [n, 4]; points: [n, 8]
+    """Owns one msm_plan handle.  Scalars: torch int64 [n, 4]; points:
+    [n, 2 w] with w = 4 (BN254) or 6 (BLS12-381) 64-bit limbs per coordinate
     (affine x limbs then y limbs, standard form, (0, 0) = infinity); the
-    result is one point, [8]."""
+    result is one point, [2 w]."""
 
     def __init__(self, max_n: int, window_bits: int = 0, curve: str = "bn254_g1"):
         self.curve = curve
         self.max_n = int(max_n)
+        self.point_words = msm_point_bytes(curve) // 8
         self.handle = msm_plan_create(curve, self.max_n, window_bits)
 
     def info(self) -> dict:
@@ -115,7 +118,7 @@ class MsmPlan:
     def execute(self, scalars, points, out=None, count: int | None = None, stream=None):
         n = scalars.shape[0] if count is None else int(count)
         if out is None:
-            out = scalars.new_empty((8,))
+            out = scalars.new_empty((self.point_words,))
         msm_execute(self.handle, scalars, points, n, out, stream)
         return out
 
@@ -140,9 +143,9 @@ class MsmPlan:
             pass
 
 
-def fixed_base_points(scalars, out=None, stream=None):
-    """points[n] = scalars[n] G on BN254 G1 (input generation for MSM)."""
+def fixed_base_points(scalars, out=None, stream=None, curve: str = "bn254_g1"):
+    """points[n] = scalars[n] G on the curve's generator (input generation for MSM)."""
     if out is None:
-        out = scalars.new_empty((scalars.shape[0], 8))
-    msm_fixed_base("bn254_g1", scalars, scalars.shape[0], out, stream)
+        out = scalars.new_empty((scalars.shape[0], msm_point_bytes(curve) // 8))
+    msm_fixed_base(curve, scalars, scalars.shape[0], out, stream)
     return out

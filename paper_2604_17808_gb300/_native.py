@@ -26,7 +26,7 @@ KIND = {"forward": 0, "inverse": 1, "coset": 2, "coset_inverse": 3}
 PATH = {"auto": 0, "butterfly": 1, "matrix": 2}
 HEADER = os.path.join(_build.ROOT, "include", "ntt_gb300.h")
 HEADERS = (HEADER, os.path.join(_build.ROOT, "include", "msm_gb300.h"))
-CURVE = {"bn254_g1": 0}
+CURVE = {"bn254_g1": 0, "bls12_381_g1": 1}
 
 
 class NttError(RuntimeError):
@@ -119,6 +119,7 @@ _SIGS = {
     "ntt_server_release": (ctypes.c_int, [_VP, _U64]),
     "ntt_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ServerStats)]),
     "ntt_server_destroy": (ctypes.c_int, [_VP]),
+    "msm_point_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_U32)]),
     "msm_plan_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _U64, _U32]),
     "msm_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(MsmPlanDesc)]),
     "msm_plan_destroy": (ctypes.c_int, [_VP]),
@@ -427,6 +428,12 @@ def ntt_field_mont_mul_rep(field, d_a, d_b, d_out, count: int, reps: int, varian
 
 def _curve(c) -> int:
     return CURVE[c] if isinstance(c, str) else int(c)
+
+
+def msm_point_bytes(curve) -> int:
+    b = _U32(0)
+    _check(load().msm_point_bytes(_curve(curve), ctypes.byref(b)), "msm_point_bytes")
+    return int(b.value)
 
 
 def msm_plan_create(curve, max_n: int, window_bits: int = 0) -> int:

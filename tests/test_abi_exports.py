@@ -74,7 +74,11 @@ def test_no_gpu_is_reported_loudly(lib):
 def test_msm_arguments_are_checked_without_touching_the_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.msm_plan_create(None, 0, 16, 0) == 1
-    assert lib.msm_plan_create(ctypes.byref(h), 1, 16, 0) == 1          # unknown curve
+    assert lib.msm_plan_create(ctypes.byref(h), 2, 16, 0) == 1          # unknown curve
+    b = ctypes.c_uint32(0)
+    assert lib.msm_point_bytes(0, ctypes.byref(b)) == 0 and b.value == 64
+    assert lib.msm_point_bytes(1, ctypes.byref(b)) == 0 and b.value == 96
+    assert lib.msm_point_bytes(2, ctypes.byref(b)) == 1
     assert lib.msm_plan_create(ctypes.byref(h), 0, (1 << 28) + 1, 0) == 2  # above MSM_MAX_POINTS
     assert lib.msm_plan_create(ctypes.byref(h), 0, 16, 23) == 2         # window too wide
     assert lib.msm_plan_create(ctypes.byref(h), 0, 1 << 25, 1) == 2     # 254 windows x 2^25 > 2^32 indices
@@ -84,6 +88,7 @@ def test_msm_arguments_are_checked_without_touching_the_gpu(lib):
     assert lib.msm_plan_info(None, None) == 1
     assert lib.msm_poll_error(None, None) == 1
     assert lib.msm_fixed_base(3, None, 4, None, None) == 1
+    assert lib.msm_fixed_base(1, None, 4, None, None) == 1
     assert lib.msm_fixed_base(0, None, 0, None, None) == 0              # nothing to do
     assert lib.msm_fixed_base(0, None, 4, None, None) == 1
 
