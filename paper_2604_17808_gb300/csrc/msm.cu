@@ -56,7 +56,6 @@
 
 #include "../../include/msm_gb300.h"
 #include "ec_xyzz.cuh"
-#include "host_field.h"
 
 namespace gb300ntt {
 namespace {

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   constexpr uint32_t E_BYTES = NCOL * K * 2;
   constexpr uint32_t A_BYTES = kMatRows * K * 2;
   static_assert(NCOL <= 256, "one MMA per K step");
+  static_assert(E_BYTES + A_BYTES <= 227u * 1024u, "E and the A tile fit in shared memory");
   extern __shared__ __align__(1024) uint8_t mat_smem[];
   uint8_t *sE = mat_smem;
   uint8_t *sA = mat_smem + E_BYTES;                   // also the output staging area

@@ -201,7 +201,8 @@ __device__ __forceinline__ void round_radix2(uint4 *tile, const uint4 *dft_tw) {
 template <class F, int LOGS, int TL>
 __device__ __forceinline__ void round_radix4(uint4 *tile, const uint4 *dft_tw, uint32_t T) {
   const uint32_t step = 1u << T;
-  const uint32_t sh = LOGS - 2 - T;
+  // (the LOGS = 1 instantiation is never called: its rounds are radix-2)
+  const uint32_t sh = static_cast<uint32_t>(LOGS - 2) - T;
 #pragma unroll 1
   for (int i = 0; i < kGroupsPerThread; ++i) {
     const uint32_t g = threadIdx.x + TileCfg<TL>::kThreads * i;   // group index
