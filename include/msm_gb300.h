@@ -99,6 +99,18 @@ ntt_status msm_execute(msm_plan plan, const void *d_scalars, const void *d_point
                        void *d_result, ntt_stream stream);
 ntt_status msm_poll_error(msm_plan plan, uint32_t *flags);
 
+/* Part of the MSM over the windows [window_begin, window_end) of the plan's
+ * signed-digit decomposition (0 <= begin <= end <= num_windows):
+ *     result = sum_{begin <= k < end} 2^(k c) W_k,
+ * W_k the window's bucket sum (Algorithm 2's window sums, already scaled by
+ * their weight).  The parts over a split of [0, num_windows) add up to the
+ * MSM (msm_execute with all-ones scalars adds points), which is how the MSM
+ * shards across GPUs: each GPU takes a range of windows, one gathers and
+ * adds the parts.  An empty range gives the point at infinity.  Same
+ * arguments, layout and errors as msm_execute otherwise. */
+ntt_status msm_execute_windows(msm_plan plan, const void *d_scalars, const void *d_points, uint64_t count,
+                               uint32_t window_begin, uint32_t window_end, void *d_result, ntt_stream stream);
+
 /* Fixed-base generation of inputs: points[n] = scalars[n] G (affine, standard
  * form; a zero scalar gives the point at infinity), any scalars < 2^256.
  * The first call per device and curve builds and keeps a comb table of 8192

@@ -7,7 +7,8 @@ include/ntt_gb300.h); this package is its thin Python binding:
   * ``_build``   -- the nvcc build of the library;
   * ``Plan``     -- a small owner object over a plan handle for torch users;
   * ``MsmPlan``  -- the same for the multi-scalar multiplication on BN254 G1
-                    or BLS12-381 G1 (C ABI in include/msm_gb300.h).
+                    or BLS12-381 G1 (C ABI in include/msm_gb300.h);
+  * ``msm_shard`` -- the MSM with its windows shared out over ranks.
 
 Importing the package does not load CUDA; the first call does, and raises if
 the library has not been built.
@@ -23,6 +24,7 @@ from ._native import (  # noqa: F401
     PATH,
     NttError,
     msm_execute,
+    msm_execute_windows,
     msm_fixed_base,
     msm_plan_create,
     msm_point_bytes,
@@ -120,6 +122,15 @@ class MsmPlan:
         if out is None:
             out = scalars.new_empty((self.point_words,))
         msm_execute(self.handle, scalars, points, n, out, stream)
+        return out
+
+    def execute_windows(self, scalars, points, window_begin: int, window_end: int, out=None,
+                        count: int | None = None, stream=None):
+        """sum over windows [begin, end) of 2^(k c) W_k (see msm_execute_windows)."""
+        n = scalars.shape[0] if count is None else int(count)
+        if out is None:
+            out = scalars.new_empty((self.point_words,))
+        msm_execute_windows(self.handle, scalars, points, n, window_begin, window_end, out, stream)
         return out
 
     def poll_error(self) -> int:

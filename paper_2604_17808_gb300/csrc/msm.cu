@@ -195,20 +195,22 @@ __global__ void __launch_bounds__(kEcThreads) msm_prepare_kernel(const uint4 *pt
   }
 }
 
-// Bucketize, pass 1: one counter per (window, digit magnitude).
+// Bucketize, pass 1: one counter per (window, digit magnitude), windows
+// [kb, ke) (the digits below kb are still recoded for their carries).
 template <class C>
 __global__ void __launch_bounds__(256) msm_count_kernel(const uint4 *__restrict__ scalars, uint64_t n, uint32_t c,
-                                                        uint32_t K, uint32_t *__restrict__ counts, MsmTotals *tot) {
+                                                        uint32_t kb, uint32_t ke, uint32_t *__restrict__ counts,
+                                                        MsmTotals *tot) {
   const uint32_t lb = c - 1;  // log2 of the buckets per window
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s[8];
     fe_load_global(s, scalars, i);
     if (!C::scalar_ok(s)) atomicOr(&tot->err, (uint32_t)MSM_ERR_SCALAR);
     uint32_t carry = 0;
-    for (uint32_t k = 0; k < K; ++k) {
+    for (uint32_t k = 0; k < ke; ++k) {
       bool neg;
       const uint32_t m = signed_digit(s, k, c, carry, neg);
-      if (m) atomicAdd(&counts[((uint64_t)k << lb) + m - 1], 1u);
+      if (m && k >= kb) atomicAdd(&counts[((uint64_t)k << lb) + m - 1], 1u);
     }
   }
 }
@@ -303,23 +305,24 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
 }
 
 // Bucketize, pass 2: each point index (sign in bit 31) into the next free
-// slot of its bucket; the atomics of eight windows are in flight at once.
+// slot of its bucket, windows [kb, ke); the atomics of eight windows are in
+// flight at once.
 __global__ void __launch_bounds__(256) msm_scatter_kernel(const uint4 *__restrict__ scalars, uint64_t n, uint32_t c,
-                                                          uint32_t K, uint32_t *__restrict__ cursor,
+                                                          uint32_t kb, uint32_t ke, uint32_t *__restrict__ cursor,
                                                           uint32_t *__restrict__ sorted) {
   const uint32_t lb = c - 1;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s[8];
     fe_load_global(s, scalars, i);
     uint32_t carry = 0;
-    for (uint32_t k0 = 0; k0 < K; k0 += 8) {
+    for (uint32_t k0 = 0; k0 < ke; k0 += 8) {
       uint32_t pos[8], val[8];
 #pragma unroll
       for (uint32_t j = 0; j < 8; ++j) {
         const uint32_t k = k0 + j;
         bool neg = false;
-        const uint32_t m = k < K ? signed_digit(s, k, c, carry, neg) : 0u;
-        pos[j] = m ? atomicAdd(&cursor[((uint64_t)k << lb) + m - 1], 1u) : 0xffffffffu;
+        const uint32_t m = k < ke ? signed_digit(s, k, c, carry, neg) : 0u;
+        pos[j] = (m && k >= kb) ? atomicAdd(&cursor[((uint64_t)k << lb) + m - 1], 1u) : 0xffffffffu;
         val[j] = (uint32_t)i | (neg ? kSignBit : 0u);
       }
 #pragma unroll
@@ -469,13 +472,14 @@ __device__ __forceinline__ void load_bucket(Xyzz<T> &p, const uint4 *bucket_sum,
 // children's W are the leaves themselves (W_j = B_j).
 template <class C>
 __global__ void __launch_bounds__(kEcThreads, C::kTreeMinBlocks)
-    msm_reduce_level_kernel(uint32_t s, uint32_t lb, uint32_t K, const uint4 *bucket_sum, const uint4 *pieces,
-                            const uint32_t *offsets, uint32_t S, uint4 *heap_w, uint4 *heap_b) {
+    msm_reduce_level_kernel(uint32_t s, uint32_t lb, uint32_t kb, uint32_t nk, const uint4 *bucket_sum,
+                            const uint4 *pieces, const uint32_t *offsets, uint32_t S, uint4 *heap_w,
+                            uint4 *heap_b) {
   using T = typename C::T;
-  const uint64_t per = 1ull << s, total = per * K;
+  const uint64_t per = 1ull << s, total = per * nk;  // windows kb .. kb + nk - 1
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = t >> s, b = t & (per - 1);
+    const uint64_t k = kb + (t >> s), b = t & (per - 1);
     const uint64_t heap0 = k << lb;  // window k's heap
     const uint64_t node = heap0 + per + b;
     Xyzz<T> a, br;
@@ -505,10 +509,11 @@ __global__ void __launch_bounds__(kEcThreads, C::kTreeMinBlocks)
   }
 }
 
-// WM: MSM = sum_k 2^(k c) W_k by Horner, then affine standard form.  With
-// one bucket per window (c = 1) W_k is that bucket.
+// WM: sum_{kb <= k < ke} 2^(k c) W_k by Horner (then kb c doublings), in
+// affine standard form; the whole MSM for [0, K).  With one bucket per
+// window (c = 1) W_k is that bucket.
 template <class C>
-__global__ void msm_merge_kernel(uint32_t c, uint32_t K, const uint4 *heap_w, const uint4 *bucket_sum,
+__global__ void msm_merge_kernel(uint32_t c, uint32_t kb, uint32_t ke, const uint4 *heap_w, const uint4 *bucket_sum,
                                  const uint4 *pieces, const uint32_t *offsets, uint32_t S,
                                  EcConst<typename C::T> kc, uint4 *result) {
   using T = typename C::T;
@@ -517,7 +522,7 @@ __global__ void msm_merge_kernel(uint32_t c, uint32_t K, const uint4 *heap_w, co
   const uint32_t lb = c - 1;
   Xyzz<T> acc;
   xyzz_set_inf(acc);
-  for (int k = (int)K - 1; k >= 0; --k) {
+  for (int k = (int)ke - 1; k >= (int)kb; --k) {
     if (!xyzz_is_inf(acc))
       for (uint32_t j = 0; j < c; ++j) xyzz_dbl(acc, acc);
     Xyzz<T> w;
@@ -525,6 +530,8 @@ __global__ void msm_merge_kernel(uint32_t c, uint32_t K, const uint4 *heap_w, co
     else load_point_xyzz(w, heap_w, ((uint64_t)k << lb) + 1);
     xyzz_add(acc, w);
   }
+  if (!xyzz_is_inf(acc))
+    for (uint32_t j = 0; j < c * kb; ++j) xyzz_dbl(acc, acc);
   uint32_t x[L], y[L];
   xyzz_to_affine_std<T>(x, y, acc, kc.one);
   T::store(result, 0, x);
@@ -830,7 +837,8 @@ const EcConst<FqBls381> &plan_const<CurveBls381>(const msm_plan p) { return p->k
 
 // The launch sequence of one MSM (all on stream st).
 template <class C>
-ntt_status enqueue_msm(msm_plan p, const uint4 *sc, const uint4 *pt, uint64_t n, uint4 *result, cudaStream_t st) {
+ntt_status enqueue_msm(msm_plan p, const uint4 *sc, const uint4 *pt, uint64_t n, uint32_t kb, uint32_t ke,
+                       uint4 *result, cudaStream_t st) {
   const auto &k = plan_const<C>(p);
   const int sms = p->sms;
   const uint32_t lb = p->c - 1;
@@ -839,13 +847,13 @@ ntt_status enqueue_msm(msm_plan p, const uint4 *sc, const uint4 *pt, uint64_t n,
   MSM_TRY(cuda_st(cudaMemsetAsync(p->tot, 0, offsetof(MsmTotals, err), st)));
   if (n > 0) {
     msm_prepare_kernel<C><<<grid_for(n, kEcThreads, sms, 16), kEcThreads, 0, st>>>(pt, n, k, p->pts_m, p->tot);
-    msm_count_kernel<C><<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, p->K, p->counts, p->tot);
+    msm_count_kernel<C><<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, kb, ke, p->counts, p->tot);
   }
   scan_reduce_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->tile_sums);
   scan_tiles_kernel<<<1, kScanThreads, 0, st>>>(p->tile_sums, p->num_tiles, p->nb, p->offsets, p->tot);
   scan_apply_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->tile_sums, p->offsets, p->cursor);
   if (n > 0) {
-    msm_scatter_kernel<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, p->K, p->cursor, p->sorted);
+    msm_scatter_kernel<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, kb, ke, p->cursor, p->sorted);
     const uint64_t segs = (n * p->K + p->S - 1) / p->S;
     const int g = grid_for(segs, kEcThreads, sms, C::kMinBlocks);
     msm_accumulate_kernel<C><<<g, kEcThreads, 0, st>>>(p->pts_m, p->sorted, p->offsets, p->nb, p->S, k, p->tot,
@@ -857,12 +865,12 @@ ntt_status enqueue_msm(msm_plan p, const uint4 *sc, const uint4 *pt, uint64_t n,
     for (uint32_t r = 0; (1ull << r) <= max_span; ++r)
       msm_combine_kernel<C><<<gt, kEcThreads, 0, st>>>(p->offsets, p->seg_ends, p->S, p->tot, r, p->pieces);
   }
-  for (int s = (int)lb - 1; s >= 0; --s) {
-    const uint64_t work = ((uint64_t)p->K) << s;
+  for (int s = (int)lb - 1; s >= 0 && ke > kb; --s) {
+    const uint64_t work = ((uint64_t)(ke - kb)) << s;
     msm_reduce_level_kernel<C><<<grid_for(work, kEcThreads, sms, C::kTreeMinBlocks), kEcThreads, 0, st>>>(
-        (uint32_t)s, lb, p->K, p->bucket_sum, p->pieces, p->offsets, p->S, p->heap_w, p->heap_b);
+        (uint32_t)s, lb, kb, ke - kb, p->bucket_sum, p->pieces, p->offsets, p->S, p->heap_w, p->heap_b);
   }
-  msm_merge_kernel<C><<<1, 32, 0, st>>>(p->c, p->K, p->heap_w, p->bucket_sum, p->pieces, p->offsets, p->S, k,
+  msm_merge_kernel<C><<<1, 32, 0, st>>>(p->c, kb, ke, p->heap_w, p->bucket_sum, p->pieces, p->offsets, p->S, k,
                                         result);
   return cuda_st(cudaGetLastError());
 }
@@ -1001,8 +1009,27 @@ ntt_status msm_execute(msm_plan p, const void *d_scalars, const void *d_points, 
   cudaStream_t st = (cudaStream_t)stream;
   const uint4 *sc = (const uint4 *)d_scalars;
   const uint4 *pt = (const uint4 *)d_points;
-  if (p->curve == MSM_CURVE_BLS12_381_G1) return enqueue_msm<CurveBls381>(p, sc, pt, n, (uint4 *)d_result, st);
-  return enqueue_msm<CurveBn254>(p, sc, pt, n, (uint4 *)d_result, st);
+  if (p->curve == MSM_CURVE_BLS12_381_G1)
+    return enqueue_msm<CurveBls381>(p, sc, pt, n, 0, p->K, (uint4 *)d_result, st);
+  return enqueue_msm<CurveBn254>(p, sc, pt, n, 0, p->K, (uint4 *)d_result, st);
+}
+
+ntt_status msm_execute_windows(msm_plan p, const void *d_scalars, const void *d_points, uint64_t n,
+                               uint32_t window_begin, uint32_t window_end, void *d_result, ntt_stream stream) {
+  if (!p || window_begin > window_end || window_end > p->K) return NTT_ERR_INVALID_ARG;
+  if (window_begin == 0 && window_end == p->K) return msm_execute(p, d_scalars, d_points, n, d_result, stream);
+  // the same argument checks as msm_execute
+  if (!d_result || n > p->max_n) return NTT_ERR_INVALID_ARG;
+  const uintptr_t pa = p->curve == MSM_CURVE_BLS12_381_G1 ? 16 : 32;
+  if ((uintptr_t)d_result % pa) return NTT_ERR_INVALID_ARG;
+  if (n > 0 && (!d_scalars || !d_points || ((uintptr_t)d_scalars % 32) || ((uintptr_t)d_points % pa)))
+    return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint4 *sc = (const uint4 *)d_scalars;
+  const uint4 *pt = (const uint4 *)d_points;
+  if (p->curve == MSM_CURVE_BLS12_381_G1)
+    return enqueue_msm<CurveBls381>(p, sc, pt, n, window_begin, window_end, (uint4 *)d_result, st);
+  return enqueue_msm<CurveBn254>(p, sc, pt, n, window_begin, window_end, (uint4 *)d_result, st);
 }
 
 ntt_status msm_poll_error(msm_plan p, uint32_t *flags) {
