@@ -4,9 +4,10 @@ base field) against the CPU oracle: the result point must be identical.
 Inputs are seeded: scalars uniform in [0, r) of BLS12-381 Fr, points
 P_n = t_n G for seeded t_n, so the expected value also has the closed form
 (sum_n S_n t_n mod r) G.  Small cases take their points from the oracle; the
-2^22-point case takes them from the library's fixed-base generator (a sample
-checked against the oracle) and checks the MSM against the closed form, in
-the benchmark's launch configuration (automatic window).
+2^22- and 2^24-point cases (the benchmark's sizes and launch configuration,
+automatic window) take them from the library's fixed-base generator, check a
+sample of them against the oracle, and check the MSM against the closed
+form.
 """
 
 from __future__ import annotations
@@ -152,10 +153,12 @@ def test_bls_fixed_base_generator(msm):
     assert got[-5] is None and got[-4] == G and got[-1] is None
 
 
-def test_bls_msm_2_22_closed_form(msm):
-    """2^22 points, automatic window: points from the fixed-base generator, 24
-    of them checked against the oracle; the MSM against the closed form."""
-    n = 1 << 22
+@pytest.mark.parametrize("log_n", [22, 24])
+def test_bls_msm_full_size_closed_form(msm, log_n):
+    """2^22 and 2^24 points (the benchmark's sizes), automatic window: points
+    from the fixed-base generator, 24 of them checked against the oracle; the
+    MSM against the closed form."""
+    n = 1 << log_n
     sw = ntt_synth.uniform_elements("bls12_381_fr", n, ntt_synth.config_seed(7))
     tw = ntt_synth.uniform_elements("bls12_381_fr", n, ntt_synth.config_seed(7, 1))
     d_t = _dev(tw)
