@@ -111,6 +111,21 @@ ntt_status msm_poll_error(msm_plan plan, uint32_t *flags);
 ntt_status msm_execute_windows(msm_plan plan, const void *d_scalars, const void *d_points, uint64_t count,
                                uint32_t window_begin, uint32_t window_end, void *d_result, ntt_stream stream);
 
+/* Precomputed bases, for points reused across calls (a prover's fixed
+ * setup points): msm_plan_set_bases checks and converts points[0..count)
+ * once and stores, for every window k, the copies 2^(k c) P_n (affine), so
+ * that msm_execute_bases(scalars) computes sum_n S_n P_n with one bucket set
+ * for all windows: one reduction tree instead of K, and no window merge.
+ * Same result as msm_execute.  Scratch: K x max_n extra points (counted in
+ * device_bytes); NTT_ERR_UNSUPPORTED when the plan has more than 32 windows
+ * (window_bits below 8 or 9) or K x max_n >= 2^31.  Invalid points set
+ * MSM_ERR_POINT and count as the point at infinity.  msm_execute_bases
+ * accepts count <= the count last set (NTT_ERR_INVALID_ARG otherwise, or
+ * before any set); both calls enqueue on `stream`. */
+ntt_status msm_plan_set_bases(msm_plan plan, const void *d_points, uint64_t count, ntt_stream stream);
+ntt_status msm_execute_bases(msm_plan plan, const void *d_scalars, uint64_t count, void *d_result,
+                             ntt_stream stream);
+
 /* Fixed-base generation of inputs: points[n] = scalars[n] G (affine, standard
  * form; a zero scalar gives the point at infinity), any scalars < 2^256.
  * The first call per device and curve builds and keeps a comb table of 8192

@@ -24,12 +24,14 @@ from ._native import (  # noqa: F401
     PATH,
     NttError,
     msm_execute,
+    msm_execute_bases,
     msm_execute_windows,
     msm_fixed_base,
     msm_plan_create,
     msm_point_bytes,
     msm_plan_destroy,
     msm_plan_info,
+    msm_plan_set_bases,
     msm_poll_error,
     ntt_batch_submit,
     ntt_coset_forward,
@@ -131,6 +133,18 @@ class MsmPlan:
         if out is None:
             out = scalars.new_empty((self.point_words,))
         msm_execute_windows(self.handle, scalars, points, n, window_begin, window_end, out, stream)
+        return out
+
+    def set_bases(self, points, count: int | None = None, stream=None) -> None:
+        """Precompute the window copies of fixed points (msm_plan_set_bases)."""
+        msm_plan_set_bases(self.handle, points, points.shape[0] if count is None else int(count), stream)
+
+    def execute_bases(self, scalars, out=None, count: int | None = None, stream=None):
+        """sum_n scalars[n] P_n over the points given to set_bases."""
+        n = scalars.shape[0] if count is None else int(count)
+        if out is None:
+            out = scalars.new_empty((self.point_words,))
+        msm_execute_bases(self.handle, scalars, n, out, stream)
         return out
 
     def poll_error(self) -> int:

@@ -126,6 +126,8 @@ _SIGS = {
     "msm_execute": (ctypes.c_int, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "msm_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
     "msm_execute_windows": (ctypes.c_int, [_VP, _VP, _VP, _U64, _U32, _U32, _VP, _VP]),
+    "msm_plan_set_bases": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "msm_execute_bases": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
     "msm_fixed_base": (ctypes.c_int, [ctypes.c_int, _VP, _U64, _VP, _VP]),
     "ntt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ntt_version": (_U32, []),
@@ -463,6 +465,15 @@ def msm_execute_windows(plan: int, d_scalars, d_points, count: int, window_begin
                         d_result, stream=None) -> None:
     _check(load().msm_execute_windows(plan, _ptr(d_scalars), _ptr(d_points), int(count), int(window_begin),
                                       int(window_end), _ptr(d_result), _stream(stream)), "msm_execute_windows")
+
+
+def msm_plan_set_bases(plan: int, d_points, count: int, stream=None) -> None:
+    _check(load().msm_plan_set_bases(plan, _ptr(d_points), int(count), _stream(stream)), "msm_plan_set_bases")
+
+
+def msm_execute_bases(plan: int, d_scalars, count: int, d_result, stream=None) -> None:
+    _check(load().msm_execute_bases(plan, _ptr(d_scalars), int(count), _ptr(d_result), _stream(stream)),
+           "msm_execute_bases")
 
 
 def msm_poll_error(plan: int) -> int:

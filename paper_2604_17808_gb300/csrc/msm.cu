@@ -197,11 +197,13 @@ __global__ void __launch_bounds__(kEcThreads) msm_prepare_kernel(const uint4 *pt
 
 // Bucketize, pass 1: one counter per (window, digit magnitude), windows
 // [kb, ke) (the digits below kb are still recoded for their carries).
+// With precomputed bases (flat = true) every window uses the same 2^(c-1)
+// buckets: the point of digit k of scalar i is the copy 2^(k c) P_i.
 template <class C>
 __global__ void __launch_bounds__(256) msm_count_kernel(const uint4 *__restrict__ scalars, uint64_t n, uint32_t c,
-                                                        uint32_t kb, uint32_t ke, uint32_t *__restrict__ counts,
-                                                        MsmTotals *tot) {
-  const uint32_t lb = c - 1;  // log2 of the buckets per window
+                                                        uint32_t kb, uint32_t ke, bool flat,
+                                                        uint32_t *__restrict__ counts, MsmTotals *tot) {
+  const uint32_t lb = flat ? 0u : c - 1;  // window stride of the bucket index (log2)
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s[8];
     fe_load_global(s, scalars, i);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256) msm_count_kernel(const uint4 *__restrict_
     for (uint32_t k = 0; k < ke; ++k) {
       bool neg;
       const uint32_t m = signed_digit(s, k, c, carry, neg);
-      if (m && k >= kb) atomicAdd(&counts[((uint64_t)k << lb) + m - 1], 1u);
+      if (m && k >= kb) atomicAdd(&counts[(flat ? 0ull : ((uint64_t)k << lb)) + m - 1], 1u);
     }
   }
 }
@@ -308,8 +310,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
 // slot of its bucket, windows [kb, ke); the atomics of eight windows are in
 // flight at once.
 __global__ void __launch_bounds__(256) msm_scatter_kernel(const uint4 *__restrict__ scalars, uint64_t n, uint32_t c,
-                                                          uint32_t kb, uint32_t ke, uint32_t *__restrict__ cursor,
+                                                          uint32_t kb, uint32_t ke, uint32_t flat_stride,
+                                                          uint32_t *__restrict__ cursor,
                                                           uint32_t *__restrict__ sorted) {
+  // flat_stride > 0: precomputed bases, one bucket set, point copy k at k * flat_stride
   const uint32_t lb = c - 1;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s[8];
@@ -322,8 +326,9 @@ __global__ void __launch_bounds__(256) msm_scatter_kernel(const uint4 *__restric
         const uint32_t k = k0 + j;
         bool neg = false;
         const uint32_t m = k < ke ? signed_digit(s, k, c, carry, neg) : 0u;
-        pos[j] = (m && k >= kb) ? atomicAdd(&cursor[((uint64_t)k << lb) + m - 1], 1u) : 0xffffffffu;
-        val[j] = (uint32_t)i | (neg ? kSignBit : 0u);
+        const uint64_t bucket = (flat_stride ? 0ull : ((uint64_t)k << lb)) + m - 1;
+        pos[j] = (m && k >= kb) ? atomicAdd(&cursor[bucket], 1u) : 0xffffffffu;
+        val[j] = ((uint32_t)i + k * flat_stride) | (neg ? kSignBit : 0u);
       }
 #pragma unroll
       for (uint32_t j = 0; j < 8; ++j)
@@ -536,6 +541,87 @@ __global__ void msm_merge_kernel(uint32_t c, uint32_t kb, uint32_t ke, const uin
   xyzz_to_affine_std<T>(x, y, acc, kc.one);
   T::store(result, 0, x);
   T::store(result, 1, y);
+}
+
+// Precomputed bases (fixed points reused across calls): for every point P_i
+// the window copies 2^(k c) P_i, k < K, in affine Montgomery form at index
+// k * stride + i; then all windows share one bucket set, and the
+// per-window reduction trees and the window merge collapse into one window.
+// The copies are normalised with one inversion per point (Montgomery's
+// simultaneous inversion over its K copies).  Neither group has a point of
+// order two, so no copy of a point other than O is O.  Invalid points are
+// flagged and become O, as in msm_prepare_kernel.
+constexpr uint32_t kMaxBaseWindows = 32;
+
+template <class C>
+__global__ void __launch_bounds__(kEcThreads) msm_bases_kernel(const uint4 *pts, uint64_t n, uint32_t c, uint32_t K,
+                                                               uint64_t stride, EcConst<typename C::T> kc,
+                                                               uint4 *bases, MsmTotals *tot) {
+  using T = typename C::T;
+  constexpr int L = T::L;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x[L], y[L];
+    T::load(x, pts, 2 * i);
+    T::load(y, pts, 2 * i + 1);
+    bool inf = fv_is_zero<L>(x) && fv_is_zero<L>(y);
+    if (!inf) {
+      bool ok = T::canonical(x) && T::canonical(y);
+      if (ok) {
+        T::mul(x, x, kc.r2);
+        T::mul(y, y, kc.r2);
+        uint32_t l[L], r[L];
+        T::mul(l, y, y);
+        T::mul(r, x, x);
+        T::mul(r, r, x);
+        T::add(r, r, kc.b3);
+        ok = fv_equal<L>(l, r);
+      }
+      if (!ok) {
+        atomicOr(&tot->err, (uint32_t)MSM_ERR_POINT);
+        inf = true;
+      }
+    }
+    if (inf) {
+      fv_zero<L>(x);
+      for (uint32_t k = 0; k < K; ++k) {
+        T::store(bases, 2 * (k * stride + i), x);
+        T::store(bases, 2 * (k * stride + i) + 1, x);
+      }
+      continue;
+    }
+    Xyzz<T> q[kMaxBaseWindows];
+    uint32_t pre[kMaxBaseWindows][L];
+    fv_copy<L>(q[0].X, x);
+    fv_copy<L>(q[0].Y, y);
+    fv_copy<L>(q[0].ZZ, kc.one);
+    fv_copy<L>(q[0].ZZZ, kc.one);
+    fv_copy<L>(pre[0], kc.one);  // ZZ ZZZ of the affine copy
+    for (uint32_t k = 1; k < K; ++k) {
+      q[k] = q[k - 1];
+      for (uint32_t j = 0; j < c; ++j) xyzz_dbl<T>(q[k], q[k]);
+      uint32_t z[L];
+      T::mul(z, q[k].ZZ, q[k].ZZZ);
+      T::mul(pre[k], pre[k - 1], z);  // prefix products of z_k = ZZ_k ZZZ_k
+    }
+    uint32_t inv[L];
+    f_inverse<T>(inv, pre[K - 1], kc.one);  // (z_0 ... z_{K-1})^-1
+    for (int k = (int)K - 1; k >= 0; --k) {
+      uint32_t ik[L], z[L], zi[L], ax[L], ay[L];
+      if (k > 0) {
+        T::mul(ik, inv, pre[k - 1]);        // z_k^-1
+        T::mul(z, q[k].ZZ, q[k].ZZZ);
+        T::mul(inv, inv, z);                // (z_0 ... z_{k-1})^-1
+      } else {
+        fv_copy<L>(ik, inv);
+      }
+      T::mul(zi, ik, q[k].ZZZ);             // ZZ^-1
+      T::mul(ax, q[k].X, zi);
+      T::mul(zi, ik, q[k].ZZ);              // ZZZ^-1
+      T::mul(ay, q[k].Y, zi);
+      T::store(bases, 2 * (k * stride + i), ax);
+      T::store(bases, 2 * (k * stride + i) + 1, ay);
+    }
+  }
 }
 
 // ------------------------------------------------- fixed-base generation
@@ -804,6 +890,8 @@ struct msm_plan_s {
   uint2 *seg_ends = nullptr;  // first and last bucket of each segment
   uint4 *bucket_sum = nullptr, *pieces = nullptr;   // nb and 2 max_segments XYZZ points
   uint4 *heap_w = nullptr, *heap_b = nullptr;       // nb XYZZ points each
+  uint4 *bases = nullptr;     // precomputed window copies: K x max_n points (msm_plan_set_bases)
+  uint64_t bases_n = 0;       // points set (0: none)
   uint64_t device_bytes = 0;
 };
 
@@ -811,7 +899,7 @@ namespace {
 
 void free_plan(msm_plan p) {
   void *bufs[] = {p->pts_m, p->counts, p->offsets, p->cursor, p->tile_sums, p->tot, p->sorted,
-                  p->seg_ends, p->bucket_sum, p->pieces, p->heap_w, p->heap_b};
+                  p->seg_ends, p->bucket_sum, p->pieces, p->heap_w, p->heap_b, p->bases};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -836,27 +924,37 @@ template <>
 const EcConst<FqBls381> &plan_const<CurveBls381>(const msm_plan p) { return p->k381; }
 
 // The launch sequence of one MSM (all on stream st).
+// flat: the plan's precomputed bases (pt unused): one bucket set for all
+// windows, the points gathered from the window copies, one reduction tree
+// and no window merge.
 template <class C>
 ntt_status enqueue_msm(msm_plan p, const uint4 *sc, const uint4 *pt, uint64_t n, uint32_t kb, uint32_t ke,
-                       uint4 *result, cudaStream_t st) {
+                       uint4 *result, cudaStream_t st, bool flat = false) {
   const auto &k = plan_const<C>(p);
   const int sms = p->sms;
   const uint32_t lb = p->c - 1;
-  MSM_TRY(cuda_st(cudaMemsetAsync(p->counts, 0, p->nb * 4, st)));
+  const uint64_t nb = flat ? (1ull << lb) : p->nb;           // buckets in use
+  const uint32_t num_tiles = (uint32_t)((nb + kScanTile - 1) / kScanTile);
+  const uint4 *pts = flat ? p->bases : p->pts_m;
+  const uint32_t tree_kb = flat ? 0 : kb, tree_ke = flat ? 1 : ke;
+  MSM_TRY(cuda_st(cudaMemsetAsync(p->counts, 0, nb * 4, st)));
   // keep the error bits (read by msm_poll_error), reset the rest
   MSM_TRY(cuda_st(cudaMemsetAsync(p->tot, 0, offsetof(MsmTotals, err), st)));
   if (n > 0) {
-    msm_prepare_kernel<C><<<grid_for(n, kEcThreads, sms, 16), kEcThreads, 0, st>>>(pt, n, k, p->pts_m, p->tot);
-    msm_count_kernel<C><<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, kb, ke, p->counts, p->tot);
+    if (!flat)
+      msm_prepare_kernel<C><<<grid_for(n, kEcThreads, sms, 16), kEcThreads, 0, st>>>(pt, n, k, p->pts_m, p->tot);
+    msm_count_kernel<C><<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, kb, ke, flat, p->counts, p->tot);
   }
-  scan_reduce_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->tile_sums);
-  scan_tiles_kernel<<<1, kScanThreads, 0, st>>>(p->tile_sums, p->num_tiles, p->nb, p->offsets, p->tot);
-  scan_apply_kernel<<<p->num_tiles, kScanThreads, 0, st>>>(p->counts, p->nb, p->tile_sums, p->offsets, p->cursor);
+  scan_reduce_kernel<<<num_tiles, kScanThreads, 0, st>>>(p->counts, nb, p->tile_sums);
+  scan_tiles_kernel<<<1, kScanThreads, 0, st>>>(p->tile_sums, num_tiles, nb, p->offsets, p->tot);
+  scan_apply_kernel<<<num_tiles, kScanThreads, 0, st>>>(p->counts, nb, p->tile_sums, p->offsets, p->cursor);
   if (n > 0) {
-    msm_scatter_kernel<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, kb, ke, p->cursor, p->sorted);
+    msm_scatter_kernel<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(sc, n, p->c, kb, ke,
+                                                                 flat ? (uint32_t)p->max_n : 0u, p->cursor,
+                                                                 p->sorted);
     const uint64_t segs = (n * p->K + p->S - 1) / p->S;
     const int g = grid_for(segs, kEcThreads, sms, C::kMinBlocks);
-    msm_accumulate_kernel<C><<<g, kEcThreads, 0, st>>>(p->pts_m, p->sorted, p->offsets, p->nb, p->S, k, p->tot,
+    msm_accumulate_kernel<C><<<g, kEcThreads, 0, st>>>(pts, p->sorted, p->offsets, nb, p->S, k, p->tot,
                                                        p->seg_ends, p->bucket_sum, p->pieces);
     // a bucket holds at most n entries, so it crosses at most ceil(n / S)
     // segment boundaries; rounds beyond the measured maximum exit at once
@@ -865,13 +963,14 @@ ntt_status enqueue_msm(msm_plan p, const uint4 *sc, const uint4 *pt, uint64_t n,
     for (uint32_t r = 0; (1ull << r) <= max_span; ++r)
       msm_combine_kernel<C><<<gt, kEcThreads, 0, st>>>(p->offsets, p->seg_ends, p->S, p->tot, r, p->pieces);
   }
-  for (int s = (int)lb - 1; s >= 0 && ke > kb; --s) {
-    const uint64_t work = ((uint64_t)(ke - kb)) << s;
+  for (int s = (int)lb - 1; s >= 0 && tree_ke > tree_kb; --s) {
+    const uint64_t work = ((uint64_t)(tree_ke - tree_kb)) << s;
     msm_reduce_level_kernel<C><<<grid_for(work, kEcThreads, sms, C::kTreeMinBlocks), kEcThreads, 0, st>>>(
-        (uint32_t)s, lb, kb, ke - kb, p->bucket_sum, p->pieces, p->offsets, p->S, p->heap_w, p->heap_b);
+        (uint32_t)s, lb, tree_kb, tree_ke - tree_kb, p->bucket_sum, p->pieces, p->offsets, p->S, p->heap_w,
+        p->heap_b);
   }
-  msm_merge_kernel<C><<<1, 32, 0, st>>>(p->c, kb, ke, p->heap_w, p->bucket_sum, p->pieces, p->offsets, p->S, k,
-                                        result);
+  msm_merge_kernel<C><<<1, 32, 0, st>>>(p->c, tree_kb, tree_ke, p->heap_w, p->bucket_sum, p->pieces, p->offsets,
+                                        p->S, k, result);
   return cuda_st(cudaGetLastError());
 }
 
@@ -1030,6 +1129,44 @@ ntt_status msm_execute_windows(msm_plan p, const void *d_scalars, const void *d_
   if (p->curve == MSM_CURVE_BLS12_381_G1)
     return enqueue_msm<CurveBls381>(p, sc, pt, n, window_begin, window_end, (uint4 *)d_result, st);
   return enqueue_msm<CurveBn254>(p, sc, pt, n, window_begin, window_end, (uint4 *)d_result, st);
+}
+
+ntt_status msm_plan_set_bases(msm_plan p, const void *d_points, uint64_t n, ntt_stream stream) {
+  if (!p || n > p->max_n) return NTT_ERR_INVALID_ARG;
+  const uintptr_t pa = p->curve == MSM_CURVE_BLS12_381_G1 ? 16 : 32;
+  if (n > 0 && (!d_points || ((uintptr_t)d_points % pa))) return NTT_ERR_INVALID_ARG;
+  if (p->K > kMaxBaseWindows || (uint64_t)p->K * p->max_n >= (1ull << 31)) return NTT_ERR_UNSUPPORTED;
+  if (!p->bases) {
+    const uint64_t bytes = (uint64_t)p->K * std::max<uint64_t>(p->max_n, 1) * 2 * p->elem_bytes;
+    MSM_TRY(cuda_st(cudaMalloc((void **)&p->bases, bytes)));
+    p->device_bytes += bytes;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  p->bases_n = 0;
+  if (n > 0) {
+    const uint4 *pt = (const uint4 *)d_points;
+    if (p->curve == MSM_CURVE_BLS12_381_G1)
+      msm_bases_kernel<CurveBls381><<<grid_for(n, kEcThreads, p->sms, 8), kEcThreads, 0, st>>>(
+          pt, n, p->c, p->K, p->max_n, p->k381, p->bases, p->tot);
+    else
+      msm_bases_kernel<CurveBn254><<<grid_for(n, kEcThreads, p->sms, 8), kEcThreads, 0, st>>>(
+          pt, n, p->c, p->K, p->max_n, p->k254, p->bases, p->tot);
+    MSM_TRY(cuda_st(cudaGetLastError()));
+  }
+  p->bases_n = n;
+  return NTT_OK;
+}
+
+ntt_status msm_execute_bases(msm_plan p, const void *d_scalars, uint64_t n, void *d_result, ntt_stream stream) {
+  if (!p || !d_result || n > p->bases_n || (n == 0 && !p->bases)) return NTT_ERR_INVALID_ARG;
+  const uintptr_t pa = p->curve == MSM_CURVE_BLS12_381_G1 ? 16 : 32;
+  if (((uintptr_t)d_result % pa) || (n > 0 && (!d_scalars || ((uintptr_t)d_scalars % 32))))
+    return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint4 *sc = (const uint4 *)d_scalars;
+  if (p->curve == MSM_CURVE_BLS12_381_G1)
+    return enqueue_msm<CurveBls381>(p, sc, nullptr, n, 0, p->K, (uint4 *)d_result, st, true);
+  return enqueue_msm<CurveBn254>(p, sc, nullptr, n, 0, p->K, (uint4 *)d_result, st, true);
 }
 
 ntt_status msm_poll_error(msm_plan p, uint32_t *flags) {

@@ -88,6 +88,8 @@ def test_msm_arguments_are_checked_without_touching_the_gpu(lib):
     assert lib.msm_plan_info(None, None) == 1
     assert lib.msm_poll_error(None, None) == 1
     assert lib.msm_execute_windows(None, None, None, 0, 0, 0, None, None) == 1
+    assert lib.msm_plan_set_bases(None, None, 0, None) == 1
+    assert lib.msm_execute_bases(None, None, 0, None, None) == 1
     assert lib.msm_fixed_base(3, None, 4, None, None) == 1
     assert lib.msm_fixed_base(1, None, 4, None, None) == 1
     assert lib.msm_fixed_base(0, None, 0, None, None) == 0              # nothing to do

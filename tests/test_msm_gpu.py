@@ -198,10 +198,16 @@ def test_msm_full_size_closed_form(msm):
     assert sample == mo.fixed_base_points(limbs_to_ints(tw[idx]))
     plan = msm.MsmPlan(n)
     try:
-        out = plan.execute(_dev(sw), pts)
+        d_s = _dev(sw)
+        out = plan.execute(d_s, pts)
         torch.cuda.synchronize()
         assert plan.poll_error() == 0
         got = mo.words_to_points(out.cpu().numpy().view(np.uint64))[0]
+        # the same MSM from precomputed bases
+        plan.set_bases(pts)
+        out_b = plan.execute_bases(d_s)
+        torch.cuda.synchronize()
+        assert torch.equal(out_b, out) and plan.poll_error() == 0
     finally:
         plan.close()
     acc = 0
