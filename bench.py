@@ -50,7 +50,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from ntt_synth import config_seed, uniform_elements  # noqa: E402
+from ntt_synth import MODULI as MODULI_R, config_seed, uniform_elements  # noqa: E402
 
 METRIC = "255-bit NTT field elements/s (BLS12-381 Fr, n=2^20, forward+inverse, butterfly path)"
 UNIT = "elements/s"
@@ -451,6 +451,63 @@ def measure_msm(torch, N, stream, reps: int, log_sizes=(22, 24), curve: str = "b
     return out
 
 
+def measure_commit(torch, N, stream, reps: int, log_n: int = 20) -> dict:
+    """A KZG-style commitment on BLS12-381, all on the GPU: inverse NTT of
+    2^log_n evaluations to coefficients, then their MSM against setup points
+    tau^i G (made by the fixed-base generator; the tests check the result
+    against the closed form f(tau) G)."""
+    n = 1 << log_n
+    d_e = to_dev(torch, uniform_elements("bls12_381_fr", n, config_seed(8, log_n)))
+    d_c = torch.empty_like(d_e)
+    # setup scalars tau^i: a seeded geometric sequence (any scalars serve for timing)
+    tau = int(uniform_elements("bls12_381_fr", 1, config_seed(8, 99))[0, 0]) | 1
+    r = MODULI_R["bls12_381_fr"]
+    pw = np.zeros((n, 4), dtype=np.uint64)
+    t = 1
+    for i in range(n):
+        pw[i, 0] = t & 0xFFFFFFFFFFFFFFFF
+        pw[i, 1] = (t >> 64) & 0xFFFFFFFFFFFFFFFF
+        pw[i, 2] = (t >> 128) & 0xFFFFFFFFFFFFFFFF
+        pw[i, 3] = t >> 192
+        t = t * tau % r
+    d_t = to_dev(torch, pw)
+    srs = torch.empty((n, 12), dtype=torch.int64, device=d_e.device)
+    N.msm_fixed_base("bls12_381_g1", d_t, n, srs, stream)
+    del d_t
+    plan = N.ntt_plan_create("bls12_381_fr", log_n)
+    msm = N.msm_plan_create("bls12_381_g1", n, 0)
+    res = torch.empty(12, dtype=torch.int64, device=d_e.device)
+    N.msm_plan_set_bases(msm, srs, n, stream)
+
+    def step(bases: bool):
+        N.ntt_inverse(plan, d_e, d_c, stream)
+        if bases:
+            N.msm_execute_bases(msm, d_c, n, res, stream)
+        else:
+            N.msm_execute(msm, d_c, srs, n, res, stream)
+
+    out = {}
+    for bases in (False, True):
+        step(bases)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            step(bases)
+            stop.record(stream)
+            stop.synchronize()
+            times.append(start.elapsed_time(stop))
+        out["with_precomputed_bases_ms" if bases else "ms"] = round(float(np.median(times)), 3)
+    out["device_error"] = N.msm_poll_error(msm)
+    N.msm_plan_destroy(msm)
+    N.ntt_plan_destroy(plan)
+    out["workload"] = (f"KZG-style commitment, BLS12-381: inverse NTT of 2^{log_n} evaluations + MSM of the "
+                       "coefficients against 2^%d setup points tau^i G, all on the device" % log_n)
+    return out
+
+
 def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
     """The same workload on the matrix-form path (tensor-core passes)."""
     plan = N.ntt_plan_create(FIELD, log_n)
@@ -833,6 +890,7 @@ def run_ours(args) -> None:
                          "quotient_step": measure_quotient(torch, N, stream, reps=5),
                          "msm_bn254": measure_msm(torch, N, stream, reps=3),
                          "msm_bls12_381": measure_msm(torch, N, stream, reps=3, curve="bls12_381_g1"),
+                         "kzg_commit_2_20": measure_commit(torch, N, stream, reps=3),
                          "serving": measure_serving(torch, N, rates=(100, 1000, 5000), seconds=0.5, min_jobs=40)}
         if world == 1 and not args.no_cpu:
             cpu = cpu_baseline(host_inputs[0])
@@ -957,8 +1015,8 @@ def run_leg(args) -> None:
           "n_2_28": lambda: measure_large(torch, N, stream, steps=3),
           "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3),
           "wide": lambda: measure_wide(torch, N, stream, steps=10),
-          "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=tuple(args.msm_log), curve=args.msm_curve)
-          }[args.leg]
+          "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=tuple(args.msm_log), curve=args.msm_curve),
+          "commit": lambda: measure_commit(torch, N, stream, reps=5)}[args.leg]
     print(json.dumps({args.leg: fn()}), flush=True)
 
 
@@ -972,7 +1030,7 @@ def main() -> None:
     ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
-    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide", "msm"],
+    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide", "msm", "commit"],
                     help="run only this secondary measurement and print its JSON (for profiling)")
     ap.add_argument("--msm-log", type=int, nargs="+", default=[22, 24, 26],
                     help="log2 point counts of the msm leg (default: the paper's 22 24 26)")
