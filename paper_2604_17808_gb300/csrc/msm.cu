@@ -41,10 +41,18 @@
 //
 // The paper streams the sorted points straight into bucket accumulation on
 // the TPU; here the sort moves 4-byte point indices and the accumulation
-// gathers the 64-byte points by index (a point is read once per window from
-// HBM; the accumulation is bound by the integer multiply pipe, not by these
-// reads).  Points are converted to Montgomery form once per call
-// (msm_prepare_kernel), which also checks that every point lies on the curve.
+// gathers the 64- or 96-byte points by index (a point is read once per
+// window from HBM; the accumulation is bound by the integer multiply pipe,
+// not by these reads).  Points are converted to Montgomery form once per
+// call (msm_prepare_kernel), which also checks that every point lies on the
+// curve.
+//
+// Two variants reuse the same kernels: a window range [kb, ke) (the count
+// and scatter kernels skip the other windows' digits, the tree and merge run
+// over the range only) gives one rank's part of a window-sharded MSM; and
+// precomputed bases (msm_bases_kernel stores every point's window copies
+// 2^(k c) P once) put all windows' digits into one bucket set ("flat" count
+// and scatter), so one tree replaces K and the window merge disappears.
 #include <cuda_runtime.h>
 
 #include <algorithm>
