@@ -1,7 +1,6 @@
-// Kernels of the BLS12-381 scalar field.
+// BLS12-381 scalar field: table generators, element-wise kernels, the matrix-form
+// pass and the field's launcher table.
 #define NTT_FIELD FieldBls12381Fr
+#define NTT_NS bls12_381
+#define NTT_PART_MISC
 #include "ntt_kernels.inl"
-
-namespace gb300ntt {
-const FieldLaunchers &launchers_bls12_381() { return kLaunchers; }
-}  // namespace gb300ntt

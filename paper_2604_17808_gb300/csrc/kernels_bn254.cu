@@ -1,7 +1,6 @@
-// Kernels of the BN254 scalar field.
+// BN254 scalar field: table generators, element-wise kernels, the matrix-form
+// pass and the field's launcher table.
 #define NTT_FIELD FieldBn254Fr
+#define NTT_NS bn254
+#define NTT_PART_MISC
 #include "ntt_kernels.inl"
-
-namespace gb300ntt {
-const FieldLaunchers &launchers_bn254() { return kLaunchers; }
-}  // namespace gb300ntt

@@ -1,9 +1,27 @@
 // ntt_kernels.inl -- kernel instantiations and launchers for one field.
-// Included by kernels_bls12_381.cu and kernels_bn254.cu with NTT_FIELD set.
+//
+// Included by the kernels_<field>*.cu files with NTT_FIELD (the field type),
+// NTT_NS (a namespace for the field's launchers) and one NTT_PART_* macro,
+// so that the kernel families of a field compile in parallel, one nvcc
+// process each:
+//   NTT_PART_PASS = 10 or 11  the pass kernels of one tile shape;
+//   NTT_PART_BATCH            the persistent batched kernel;
+//   NTT_PART_MISC             table generators, element-wise kernels, the
+//                             matrix-form pass and the launcher table.
 #include "../../include/ntt_gb300.h"
 #include "ntt_launch.h"
 
 namespace gb300ntt {
+namespace NTT_NS {
+
+// launchers defined by the other parts of this field
+cudaError_t prepare_pass10();
+cudaError_t prepare_pass11();
+cudaError_t pass10(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st);
+cudaError_t pass11(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st);
+cudaError_t prepare_batch();
+cudaError_t batch(const BatchLaunch &b, cudaStream_t st);
+
 namespace {
 
 using F = NTT_FIELD;
@@ -12,81 +30,6 @@ __device__ __forceinline__ void fe_from_param(uint32_t r[8], const Fe32 &a) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) r[j] = a.w[j];
 }
-
-// acc *= base^e using the ladder pw (bits of e below 32).
-__device__ __forceinline__ void ladder_mul(uint32_t acc[8], uint64_t e, const Pow2Table &pw) {
-  for (int b = 0; b < 32 && (e >> b) != 0; ++b) {
-    if ((e >> b) & 1) {
-      uint32_t w[8];
-      fe_from_param(w, pw.v[b]);
-      mont_mul<F>(acc, acc, w);
-    }
-  }
-}
-
-__global__ void gen_2d_kernel(uint4 *out, uint32_t log_s, uint32_t log_mp, const Pow2Table pw,
-                              const uint4 *fac, const Fe32 init) {
-  const uint64_t total = 1ull << (log_s + log_mp);
-  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t n = idx >> log_mp, q = idx & ((1ull << log_mp) - 1);
-    uint32_t acc[8];
-    fe_from_param(acc, init);
-    if (fac) {
-      uint32_t f[8];
-      fe_load_global(f, fac, n);
-      mont_mul<F>(acc, acc, f);
-    }
-    ladder_mul(acc, n * q, pw);
-    fe_store_global(out, idx, acc);
-  }
-}
-
-__global__ void gen_1d_kernel(uint4 *out, uint64_t count, const Pow2Table pw, const Fe32 init) {
-  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
-       idx += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t acc[8];
-    fe_from_param(acc, init);
-    ladder_mul(acc, idx, pw);
-    fe_store_global(out, idx, acc);
-  }
-}
-
-__global__ void mul_vec_kernel(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count) {
-  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
-       idx += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t x[8], y[8];
-    fe_load_global(x, a, idx);
-    fe_load_global(y, b, idx);
-    mont_mul<F>(x, x, y);
-    fe_store_global(out, idx, x);
-  }
-}
-
-// Pointwise quotient of a prover on coset evaluations:
-//   out[i] = (a[i] b[i] - c[i]) z[i mod len]
-// in one pass over the vectors (3 reads, 1 write, two products and one
-// reduction per element): u = a b 2^-256, v = c 2^-256, and the multiplier
-// z 2^512 turns (u - v) back into standard form.
-__global__ void quotient_kernel(uint4 *out, const uint4 *a, const uint4 *b, const uint4 *c, const QuotientZ z,
-                                uint64_t count) {
-  const uint64_t zmask = z.len - 1;
-  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
-       idx += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t x[8], y[8], w[8];
-    fe_load_global(x, a, idx);
-    fe_load_global(y, b, idx);
-    mont_mul<F>(x, x, y);          // a b 2^-256
-    fe_load_global(y, c, idx);
-    mont_redc<F>(y, y);            // c 2^-256
-    sub_mod<F>(x, x, y);
-    fe_from_param(w, z.z[idx & zmask]);
-    mont_mul<F>(x, x, w);          // (a b - c) z
-    fe_store_global(out, idx, x);
-  }
-}
-
-// ------------------------------------------------- persistent batch kernel
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -100,12 +43,132 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
   return v;
 }
 
+}  // namespace
+
+#if defined(NTT_PART_PASS)
+
+namespace {
+
+// The fused tile is instantiated for the 1024-element tile only: that is
+// the shape of the one-wave passes it is chosen for (sizes up to 2^20).
+template <int LOGS, int TL>
+constexpr bool has_fused() {
+  return TL == 10 && LOGS >= 4;
+}
+
+template <int LOGS, int MODE, int TL>
+cudaError_t set_pass_attr() {
+  cudaError_t e = cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<TL>::kBytes);
+  if constexpr (has_fused<LOGS, TL>()) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TileCfg<TL>::kBytes);
+  }
+  return e;
+}
+
+template <int LOGS, int TL>
+cudaError_t set_pass_attrs() {
+  cudaError_t e = set_pass_attr<LOGS, kModeInner, TL>();
+  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirst, TL>();
+  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirstPre, TL>();
+  return e;
+}
+
+template <int TL>
+cudaError_t set_all_pass_attrs() {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = set_pass_attrs<1, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<2, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<3, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<4, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<5, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<6, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<7, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<8, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<9, TL>();
+  if (e == cudaSuccess) e = set_pass_attrs<10, TL>();
+  if constexpr (TL >= 11) {
+    if (e == cudaSuccess) e = set_pass_attrs<11, TL>();
+  }
+  return e;
+}
+
+template <int LOGS, int TL, bool FUSED>
+cudaError_t pass_launch(int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  const dim3 grid((unsigned)tiles), block(TileCfg<TL>::kThreads);
+  const int smem = TileCfg<TL>::kBytes;
+  switch (mode) {
+    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner, TL, FUSED><<<grid, block, smem, st>>>(a); break;
+    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst, TL, FUSED><<<grid, block, smem, st>>>(a); break;
+    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre, TL, FUSED><<<grid, block, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int LOGS, int TL>
+cudaError_t pass_logs(int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  if constexpr (has_fused<LOGS, TL>()) {
+    if (fused) return pass_launch<LOGS, TL, true>(mode, a, tiles, st);
+  }
+  return pass_launch<LOGS, TL, false>(mode, a, tiles, st);
+}
+
+template <int TL>
+cudaError_t pass_tl(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  switch (logs) {
+    case 1: return pass_logs<1, TL>(mode, fused, a, tiles, st);
+    case 2: return pass_logs<2, TL>(mode, fused, a, tiles, st);
+    case 3: return pass_logs<3, TL>(mode, fused, a, tiles, st);
+    case 4: return pass_logs<4, TL>(mode, fused, a, tiles, st);
+    case 5: return pass_logs<5, TL>(mode, fused, a, tiles, st);
+    case 6: return pass_logs<6, TL>(mode, fused, a, tiles, st);
+    case 7: return pass_logs<7, TL>(mode, fused, a, tiles, st);
+    case 8: return pass_logs<8, TL>(mode, fused, a, tiles, st);
+    case 9: return pass_logs<9, TL>(mode, fused, a, tiles, st);
+    case 10: return pass_logs<10, TL>(mode, fused, a, tiles, st);
+    case 11:
+      if constexpr (TL >= 11) return pass_logs<11, TL>(mode, fused, a, tiles, st);
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+#if NTT_PART_PASS == 10
+cudaError_t prepare_pass10() { return set_all_pass_attrs<10>(); }
+cudaError_t pass10(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  return pass_tl<10>(logs, mode, fused, a, tiles, st);
+}
+#else
+cudaError_t prepare_pass11() { return set_all_pass_attrs<11>(); }
+cudaError_t pass11(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
+  return pass_tl<11>(logs, mode, fused, a, tiles, st);
+}
+#endif
+
+#elif defined(NTT_PART_BATCH)
+
+namespace {
+
+// One tile of one segment.  Each (size, mode) variant is a separate,
+// non-inlined function: the call costs nothing next to a 2048-element tile,
+// and ptxas then compiles 33 small functions instead of one kernel holding
+// every variant inline (which took minutes).
+template <int LOGS, int MODE>
+__device__ __noinline__ void batch_tile_fn(const BatchSeg &sg, uint64_t tile, uint4 *smem) {
+  pass_tile<F, LOGS, MODE, true, 11, true>(sg.a, tile, smem);
+}
+
 template <int LOGS>
 __device__ __forceinline__ void batch_tile_logs(const BatchSeg &sg, uint64_t tile, uint4 *smem) {
   switch (sg.mode) {
-    case kModeInner: pass_tile<F, LOGS, kModeInner, true, 11, true>(sg.a, tile, smem); break;
-    case kModeFirst: pass_tile<F, LOGS, kModeFirst, true, 11, true>(sg.a, tile, smem); break;
-    default: pass_tile<F, LOGS, kModeFirstPre, true, 11, true>(sg.a, tile, smem); break;
+    case kModeInner: batch_tile_fn<LOGS, kModeInner>(sg, tile, smem); break;
+    case kModeFirst: batch_tile_fn<LOGS, kModeFirst>(sg, tile, smem); break;
+    default: batch_tile_fn<LOGS, kModeFirstPre>(sg, tile, smem); break;
   }
 }
 
@@ -181,9 +244,93 @@ __global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) batch_kernel(con
   }
 }
 
+}  // namespace
+
 cudaError_t batch(const BatchLaunch &b, cudaStream_t st) {
   batch_kernel<<<b.grid, kPassThreads, kTileBytes, st>>>(b);
   return cudaGetLastError();
+}
+
+
+cudaError_t prepare_batch() {
+  return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
+}
+
+#elif defined(NTT_PART_MISC)
+
+namespace {
+
+// acc *= base^e using the ladder pw (bits of e below 32).
+__device__ __forceinline__ void ladder_mul(uint32_t acc[8], uint64_t e, const Pow2Table &pw) {
+  for (int b = 0; b < 32 && (e >> b) != 0; ++b) {
+    if ((e >> b) & 1) {
+      uint32_t w[8];
+      fe_from_param(w, pw.v[b]);
+      mont_mul<F>(acc, acc, w);
+    }
+  }
+}
+
+__global__ void gen_2d_kernel(uint4 *out, uint32_t log_s, uint32_t log_mp, const Pow2Table pw,
+                              const uint4 *fac, const Fe32 init) {
+  const uint64_t total = 1ull << (log_s + log_mp);
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t n = idx >> log_mp, q = idx & ((1ull << log_mp) - 1);
+    uint32_t acc[8];
+    fe_from_param(acc, init);
+    if (fac) {
+      uint32_t f[8];
+      fe_load_global(f, fac, n);
+      mont_mul<F>(acc, acc, f);
+    }
+    ladder_mul(acc, n * q, pw);
+    fe_store_global(out, idx, acc);
+  }
+}
+
+__global__ void gen_1d_kernel(uint4 *out, uint64_t count, const Pow2Table pw, const Fe32 init) {
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t acc[8];
+    fe_from_param(acc, init);
+    ladder_mul(acc, idx, pw);
+    fe_store_global(out, idx, acc);
+  }
+}
+
+__global__ void mul_vec_kernel(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count) {
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x[8], y[8];
+    fe_load_global(x, a, idx);
+    fe_load_global(y, b, idx);
+    mont_mul<F>(x, x, y);
+    fe_store_global(out, idx, x);
+  }
+}
+
+// Pointwise quotient of a prover on coset evaluations:
+//   out[i] = (a[i] b[i] - c[i]) z[i mod len]
+// in one pass over the vectors (3 reads, 1 write, two products and one
+// reduction per element): u = a b 2^-256, v = c 2^-256, and the multiplier
+// z 2^512 turns (u - v) back into standard form.
+__global__ void quotient_kernel(uint4 *out, const uint4 *a, const uint4 *b, const uint4 *c, const QuotientZ z,
+                                uint64_t count) {
+  const uint64_t zmask = z.len - 1;
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t x[8], y[8], w[8];
+    fe_load_global(x, a, idx);
+    fe_load_global(y, b, idx);
+    mont_mul<F>(x, x, y);          // a b 2^-256
+    fe_load_global(y, c, idx);
+    mont_redc<F>(y, y);            // c 2^-256
+    sub_mod<F>(x, x, y);
+    fe_from_param(w, z.z[idx & zmask]);
+    mont_mul<F>(x, x, w);          // (a b - c) z
+    fe_store_global(out, idx, x);
+  }
 }
 
 // out[i] = a[i] * (b[i] * 2^-256)^reps: `reps` dependent Montgomery products
@@ -212,52 +359,6 @@ __global__ void mul_rep_coop_kernel(uint32_t *out, const uint32_t *a, const uint
   const uint32_t y = live ? b[elem * 8 + j] : 0u;
   for (uint32_t r = 0; r < reps; ++r) x = mont_mul_coop<F>(x, y, j);
   if (live) out[elem * 8 + j] = x;
-}
-
-// The fused tile is instantiated for the 1024-element tile only: that is
-// the shape of the one-wave passes it is chosen for (sizes up to 2^20).
-template <int LOGS, int TL>
-constexpr bool has_fused() {
-  return TL == 10 && LOGS >= 4;
-}
-
-template <int LOGS, int MODE, int TL>
-cudaError_t set_pass_attr() {
-  cudaError_t e = cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<TL>::kBytes);
-  if constexpr (has_fused<LOGS, TL>()) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ntt_pass_kernel<F, LOGS, MODE, TL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               TileCfg<TL>::kBytes);
-  }
-  return e;
-}
-
-template <int LOGS, int TL>
-cudaError_t set_pass_attrs() {
-  cudaError_t e = set_pass_attr<LOGS, kModeInner, TL>();
-  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirst, TL>();
-  if (e == cudaSuccess) e = set_pass_attr<LOGS, kModeFirstPre, TL>();
-  return e;
-}
-
-template <int TL>
-cudaError_t set_all_pass_attrs() {
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = set_pass_attrs<1, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<2, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<3, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<4, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<5, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<6, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<7, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<8, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<9, TL>();
-  if (e == cudaSuccess) e = set_pass_attrs<10, TL>();
-  if constexpr (TL >= 11) {
-    if (e == cudaSuccess) e = set_pass_attrs<11, TL>();
-  }
-  return e;
 }
 
 template <int LOGS, int MODE>
@@ -296,60 +397,18 @@ cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, uint32_t g
 }
 
 cudaError_t prepare() {
-  cudaError_t e = set_all_pass_attrs<11>();
+  cudaError_t e = prepare_pass11();
   if (e == cudaSuccess) e = set_matrix_attrs<1>();
   if (e == cudaSuccess) e = set_matrix_attrs<2>();
   if (e == cudaSuccess) e = set_matrix_attrs<3>();
-  if (e == cudaSuccess) e = set_all_pass_attrs<10>();
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
+  if (e == cudaSuccess) e = prepare_pass10();
+  if (e == cudaSuccess) e = prepare_batch();
   return e;
 }
 
-template <int LOGS, int TL, bool FUSED>
-cudaError_t pass_launch(int mode, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
-  const dim3 grid((unsigned)tiles), block(TileCfg<TL>::kThreads);
-  const int smem = TileCfg<TL>::kBytes;
-  switch (mode) {
-    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner, TL, FUSED><<<grid, block, smem, st>>>(a); break;
-    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst, TL, FUSED><<<grid, block, smem, st>>>(a); break;
-    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre, TL, FUSED><<<grid, block, smem, st>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-template <int LOGS, int TL>
-cudaError_t pass_logs(int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
-  if constexpr (has_fused<LOGS, TL>()) {
-    if (fused) return pass_launch<LOGS, TL, true>(mode, a, tiles, st);
-  }
-  return pass_launch<LOGS, TL, false>(mode, a, tiles, st);
-}
-
-template <int TL>
-cudaError_t pass_tl(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
-  switch (logs) {
-    case 1: return pass_logs<1, TL>(mode, fused, a, tiles, st);
-    case 2: return pass_logs<2, TL>(mode, fused, a, tiles, st);
-    case 3: return pass_logs<3, TL>(mode, fused, a, tiles, st);
-    case 4: return pass_logs<4, TL>(mode, fused, a, tiles, st);
-    case 5: return pass_logs<5, TL>(mode, fused, a, tiles, st);
-    case 6: return pass_logs<6, TL>(mode, fused, a, tiles, st);
-    case 7: return pass_logs<7, TL>(mode, fused, a, tiles, st);
-    case 8: return pass_logs<8, TL>(mode, fused, a, tiles, st);
-    case 9: return pass_logs<9, TL>(mode, fused, a, tiles, st);
-    case 10: return pass_logs<10, TL>(mode, fused, a, tiles, st);
-    case 11:
-      if constexpr (TL >= 11) return pass_logs<11, TL>(mode, fused, a, tiles, st);
-      return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 cudaError_t pass(int logs, int mode, int tl, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st) {
-  if (tl == 11) return pass_tl<11>(logs, mode, fused, a, tiles, st);
-  if (tl == 10) return pass_tl<10>(logs, mode, fused, a, tiles, st);
+  if (tl == 11) return pass11(logs, mode, fused, a, tiles, st);
+  if (tl == 10) return pass10(logs, mode, fused, a, tiles, st);
   return cudaErrorInvalidValue;
 }
 
@@ -396,4 +455,10 @@ cudaError_t quotient(uint4 *out, const uint4 *a, const uint4 *b, const uint4 *c,
 const FieldLaunchers kLaunchers = {prepare, pass, gen_2d, gen_1d, mul_vec, batch, mul_rep, matrix_pass, quotient};
 
 }  // namespace
+
+const FieldLaunchers &launchers() { return kLaunchers; }
+
+#endif
+
+}  // namespace NTT_NS
 }  // namespace gb300ntt

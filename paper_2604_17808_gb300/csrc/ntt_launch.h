@@ -1,7 +1,7 @@
 // ntt_launch.h -- host-side launchers of the per-field kernels.
 //
-// Each field's kernels are instantiated in its own translation unit
-// (kernels_bls12_381.cu, kernels_bn254.cu) so that the two compile in
+// Each field's kernels are instantiated in translation units of their own
+// (kernels_<field>*.cu, one per kernel family) so that they compile in
 // parallel; the plan code dispatches on the field id.
 #pragma once
 
@@ -81,11 +81,15 @@ struct FieldLaunchers {
                           uint64_t count, cudaStream_t st);
 };
 
-const FieldLaunchers &launchers_bls12_381();
-const FieldLaunchers &launchers_bn254();
+namespace bls12_381 {
+const FieldLaunchers &launchers();
+}
+namespace bn254 {
+const FieldLaunchers &launchers();
+}
 
 inline const FieldLaunchers &launchers(int field) {
-  return field == 0 ? launchers_bls12_381() : launchers_bn254();
+  return field == 0 ? bls12_381::launchers() : bn254::launchers();
 }
 
 }  // namespace gb300ntt
