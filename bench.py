@@ -19,12 +19,18 @@ Printed as ONE JSON line on rank 0, with
     when it has one); peak = 152 SMs * 64 IMAD/clk * 2.07 GHz;
   * e2e: the same metric through ntt_transform_host (pinned host buffers,
     host-to-device and device-to-host copies inside the timed region);
-  * cpu_baseline: the C oracle on this host's cores (single-threaded) on a
-    bounded sample of the same workload;
+  * cpu_baseline: the C oracle on this host's cores on a bounded sample of
+    the same workload: single-threaded (the value) and with each stage's
+    butterflies over every core (all_cores, plus one 2^24 transform), with
+    the host's core count;
   * secondary: the 2^24-point BLS12-381 forward NTT (elements/s and IMAD
-    roofline fraction of the whole transform), and the batched workload (64
+    roofline fraction of the whole transform), 2^28, the BN254 2^24 coset
+    transform on both paths, the wider fields, the batched workload (64
     forward NTTs of 2^14..2^22 points) as one persistent launch vs one
-    transform per call;
+    transform per call, the multiply alone, a prover's quotient step, and
+    the serving sweep (five offered rates, sampled results compared with
+    the same transform run alone); the MSM and commitment legs run only
+    with --leg;
   * clocks: nvidia-smi samples taken during the timed region.
 
 ``--impl reference`` times the oracle instead (rank 0 only), the baseline
@@ -61,6 +67,7 @@ SM_MAX_MHZ = 2070.0
 FIELD = "bls12_381_fr"
 LOG_N = 20
 ROTATE = 8
+SERVING_RATES = (100, 300, 1000, 3000, 5000)  # offered jobs/s of the serving sweep
 L2_NOTE = "inputs larger than L2: 8 rotating 2^20 vectors (in, out, round trip: 768 MiB)"
 
 
@@ -719,17 +726,22 @@ def measure_batched(torch, N, stream, reps: int) -> dict:
 
 
 def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int = 12, log_max: int = 24,
-                    seed: int = 0x5EED0005, max_inflight: int = 8, max_batch_jobs: int = 16) -> dict:
+                    seed: int = 0x5EED0005, max_inflight: int = 8, max_batch_jobs: int = 16,
+                    check: bool = False, check_per_rate: int = 3, check_max_log: int = 18) -> dict:
     """Poisson arrivals of mixed forward/inverse/coset requests over both
     fields, log2 n uniform on {log_min..log_max}, through the serving runtime
     (host buffers in, host buffers out).  Per rate: p50/p99 latency
-    (finish - arrive) and elements/s over the run."""
+    (finish - arrive) and elements/s over the run.  Every request of a size
+    reads the same pinned input; outputs go to one shared pinned buffer per
+    size, except for up to check_per_rate requests per rate (sizes up to
+    2^check_max_log) which get buffers of their own and, with check=True,
+    are compared with the same transform run alone (ntt_execute) after the
+    rate's run: each result must be the same in the mix as alone."""
     import random
 
     server = N.ntt_server_create(memory_budget_bytes=64 << 30, min_log_n=log_min, max_log_n=log_max,
                                  max_inflight=max_inflight, max_batch_jobs=max_batch_jobs)
     try:
-        # one pinned input and output buffer per (field, size), reused by every request
         bufs = {}
         for fi, field in enumerate(("bls12_381_fr", "bn254_fr")):
             for ln in range(log_min, log_max + 1):
@@ -738,9 +750,11 @@ def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int
                 bufs[(field, ln)] = (h_in, torch.empty_like(h_in).pin_memory())
         out = []
         rng = random.Random(seed)
+        checked_total, mismatches = 0, 0
         for rate in rates:
             n_jobs = max(min_jobs, int(rate * seconds))
             tickets = []
+            checks = []
             elements = 0
             t_next = time.perf_counter()
             for _ in range(n_jobs):
@@ -751,6 +765,9 @@ def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int
                 kind = rng.choice(("forward", "inverse", "coset"))
                 ln = rng.randint(log_min, log_max)
                 h_in, h_out = bufs[(field, ln)]
+                if check and len(checks) < check_per_rate and ln <= check_max_log:
+                    h_out = torch.empty_like(h_in).pin_memory()
+                    checks.append((field, kind, ln, h_in, h_out))
                 tickets.append(N.ntt_server_submit(server, field, kind, ln, h_in, h_out))
                 elements += 1 << ln
             lat, first, last = [], None, None
@@ -762,16 +779,37 @@ def measure_serving(torch, N, rates, seconds: float, min_jobs: int, log_min: int
                 last = f if last is None else max(last, f)
                 N.ntt_server_release(server, t)
             lat.sort()
-            out.append({"rate_per_s": rate, "jobs": n_jobs, "elements": elements,
-                        "elements_per_s": elements / (last - first),
-                        "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
-                        "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)})
+            row = {"rate_per_s": rate, "jobs": n_jobs, "elements": elements,
+                   "window_s": round(last - first, 3), "elements_per_s": elements / (last - first),
+                   "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
+                   "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)}
+            if check:
+                same = 0
+                for field, kind, ln, h_in, h_out in checks:
+                    plan = N.ntt_plan_create(field, ln, coset=True)
+                    try:
+                        d_x = h_in.cuda()
+                        d_y = torch.empty_like(d_x)
+                        N.ntt_execute(plan, kind, d_x, d_y)
+                        torch.cuda.synchronize()
+                        same += int(torch.equal(d_y.cpu(), h_out))
+                    finally:
+                        N.ntt_plan_destroy(plan)
+                row["checked"] = len(checks)
+                row["same_as_alone"] = same
+                checked_total += len(checks)
+                mismatches += len(checks) - same
+            out.append(row)
         stats = N.ntt_server_get_stats(server)
-        return {"workload": f"Poisson arrivals, kinds forward/inverse/coset, fields BLS12-381/BN254, "
-                            f"log2 n uniform on {{{log_min}..{log_max}}}, 64 GiB budget, {max_inflight} streams, "
-                            f"at most {max_batch_jobs} jobs per batch",
-                "rates": out, "batches": stats["batches"], "peak_device_bytes": stats["peak_device_bytes"],
-                "resident_bytes": stats["resident_bytes"]}
+        res = {"workload": f"Poisson arrivals, kinds forward/inverse/coset, fields BLS12-381/BN254, "
+                           f"log2 n uniform on {{{log_min}..{log_max}}}, 64 GiB budget, {max_inflight} streams, "
+                           f"at most {max_batch_jobs} jobs per batch",
+               "rates": out, "batches": stats["batches"], "peak_device_bytes": stats["peak_device_bytes"],
+               "resident_bytes": stats["resident_bytes"]}
+        if check:
+            res["results_checked"] = checked_total
+            res["results_same_as_alone"] = checked_total - mismatches
+        return res
     finally:
         N.ntt_server_destroy(server)
 
@@ -814,22 +852,52 @@ def measure_e2e(torch, N, x_host: np.ndarray, steps: int, log_n: int, num_lanes:
             "how": f"ntt_transform_host_async, pinned host buffers, {num_lanes} streams, wall clock"}
 
 
-def cpu_baseline(x: np.ndarray, budget_s: float = 12.0) -> dict:
-    import oracle
-
+def _oracle_rate(oracle, x: np.ndarray, budget_s: float, kinds=("forward", "inverse")) -> tuple[float, int, float]:
+    """Elements/s of the C oracle transforming x (each kind once per round)
+    until budget_s has passed (at least one round): (rate, rounds, seconds)."""
     n = x.shape[0]
     t0 = time.perf_counter()
-    done = 0
+    rounds = 0
     while True:
-        y = oracle.c_transform(FIELD, "forward", x)
-        oracle.c_transform(FIELD, "inverse", y)
-        done += 2 * n
+        y = x
+        for kind in kinds:
+            y = oracle.c_transform(FIELD, kind, y)
+        rounds += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return len(kinds) * n * rounds / dt, rounds, dt
+
+
+def cpu_baseline(x: np.ndarray, budget_s: float = 8.0, with_2_24: bool = True) -> dict:
+    """The C oracle on this host's cores: single-threaded (the headline
+    baseline value), and with the butterflies of each stage split over every
+    core OpenMP sees (same arithmetic), on the 2^20 workload vector, plus one
+    2^24-point forward transform on all cores."""
+    import oracle
+
+    host_cores = len(os.sched_getaffinity(0))
+    n = x.shape[0]
+    try:
+        oracle.c_set_threads(1)
+        v1, r1, t1 = _oracle_rate(oracle, x, budget_s)
+        threads = oracle.c_set_threads(0)
+        vall, rall, tall = _oracle_rate(oracle, x, budget_s / 2)
+        big = None
+        if with_2_24:
+            xb = uniform_elements(FIELD, 1 << 24, config_seed(3, 100))
+            vb, _, tb = _oracle_rate(oracle, xb, 0.0, kinds=("forward",))
+            big = {"value": vb, "unit": UNIT, "cores": threads, "seconds": round(tb, 2),
+                   "sample": "one forward transform of the 2^24-point BLS12-381 vector, all cores"}
+    finally:
+        oracle.c_set_threads(1)
+    return {"value": v1, "unit": UNIT, "cores": 1, "host_cores": host_cores, "kind": "oracle",
             "sample": f"C oracle (single-threaded), forward+inverse of the 2^{n.bit_length() - 1} "
-                      f"BLS12-381 workload vector, {done // (2 * n)} round(s) in {dt:.1f} s"}
+                      f"BLS12-381 workload vector, {r1} round(s) in {t1:.1f} s",
+            "all_cores": {"value": vall, "unit": UNIT, "cores": threads, "host_cores": host_cores,
+                          "sample": f"C oracle, butterflies of each stage over {threads} OpenMP threads, "
+                                    f"forward+inverse of the same vector, {rall} round(s) in {tall:.1f} s"},
+            "all_cores_2_24": big}
 
 
 def run_ours(args) -> None:
@@ -927,10 +995,8 @@ def run_ours(args) -> None:
                          "batched": measure_batched(torch, N, stream, reps=5),
                          "modmul": measure_modmul(torch, N, stream),
                          "quotient_step": measure_quotient(torch, N, stream, reps=5),
-                         "msm_bn254": measure_msm(torch, N, stream, reps=3),
-                         "msm_bls12_381": measure_msm(torch, N, stream, reps=3, curve="bls12_381_g1"),
-                         "kzg_commit_2_20": measure_commit(torch, N, stream, reps=3),
-                         "serving": measure_serving(torch, N, rates=(100, 1000, 5000), seconds=0.5, min_jobs=40)}
+                         "serving": measure_serving(torch, N, rates=SERVING_RATES, seconds=0.5, min_jobs=200,
+                                                    check=True)}
         if world == 1 and not args.no_cpu:
             cpu = cpu_baseline(host_inputs[0])
     N.ntt_plan_destroy(plan)
@@ -1040,7 +1106,7 @@ def run_serving_sweep(args) -> None:
 
     torch.cuda.set_device(0)
     N.load(build_if_missing=True)
-    res = measure_serving(torch, N, rates=(100, 300, 1000, 3000, 5000), seconds=10.0, min_jobs=2000)
+    res = measure_serving(torch, N, rates=SERVING_RATES, seconds=10.0, min_jobs=2000, check=True)
     print(json.dumps({"metric": "serving p50/p99 latency and elements/s", "serving": res}), flush=True)
 
 

@@ -165,11 +165,15 @@ ntt_status ntt_transform_host_async(ntt_plan plan, ntt_kind kind, const void *h_
  * pass's sub-transforms (up to 4), and the number of kernel launches one
  * transform makes.
  */
+/* Most passes a transform is split into (the matrix path splits 2^28 into
+ * ten passes of at most 2^3 points). */
+#define NTT_MAX_PASSES 12
+
 typedef struct ntt_plan_desc {
     uint32_t field;
     uint32_t log_n;
     uint32_t num_passes;
-    uint32_t pass_log[4];
+    uint32_t pass_log[NTT_MAX_PASSES];
     uint32_t launches_per_transform;
     uint32_t path;
     uint64_t device_bytes;
@@ -206,13 +210,27 @@ ntt_status ntt_plan_read_table(ntt_plan plan, ntt_kind kind, uint32_t pass, uint
 typedef struct ntt_tune_result {
     uint32_t path;            /* ntt_path chosen */
     uint32_t num_passes;      /* butterfly passes (the matrix path has its own split) */
-    uint32_t pass_log[4];
-    uint32_t tile_log[4];     /* log2 of each pass's tile (10 or 11) */
+    uint32_t pass_log[NTT_MAX_PASSES];
+    uint32_t tile_log[NTT_MAX_PASSES];  /* log2 of each pass's tile (10 or 11) */
     uint32_t candidates;
     double best_ms;           /* forward transform, winner */
     double default_ms;        /* forward transform, configuration before tuning */
 } ntt_tune_result;
 ntt_status ntt_plan_autotune(ntt_plan plan, uint32_t reps, ntt_tune_result *result);
+
+/*
+ * Rebuild the plan's butterfly path for an explicit pass split: num_passes
+ * (1..NTT_MAX_PASSES) sub-transform sizes 2^pass_log[j] (each 1..11, summing
+ * to log_n; pass 0 transforms the digit of largest stride, Sec. 3.3.2's
+ * 3-/5-step decomposition with P passes), passes of at most 2^10 points on
+ * tiles of 2^tile_log elements (10 or 11; larger passes always use 11).  The
+ * plan's tables are rebuilt (coset shift kept) and its path set to
+ * NTT_PATH_BUTTERFLY; cached batched job lists that use the plan are
+ * dropped.  This is the autotuner's own step, for callers (and tests) that
+ * choose a split themselves.  Synchronous; NTT_ERR_INVALID_ARG for a split
+ * that does not fit these rules.
+ */
+ntt_status ntt_plan_set_passes(ntt_plan plan, uint32_t num_passes, const uint32_t *pass_log, uint32_t tile_log);
 
 /*
  * Batched submission (the paper batches NTTs to fill its matrix units,
@@ -260,22 +278,31 @@ ntt_status ntt_batch_submit(const ntt_job *jobs, size_t n, ntt_stream stream);
  * or other allocating routine; the caller passes the plans (created
  * beforehand) and the input and output buffers, as for ntt_batch_submit.
  *
- * Limits: at most 64 jobs per call (NTT_ERR_UNSUPPORTED beyond); same job
- * rules as ntt_batch_submit (in != out, butterfly-path plans, no overlap).
- * d_status: device pointer to one uint32_t (4-byte aligned) set to 0 at the
+ * Limits: at most 64 jobs per call and at most 256 passes of jobs per field
+ * (the jobs' pass counts summed; NTT_ERR_UNSUPPORTED beyond, nothing
+ * launched); same job rules as ntt_batch_submit (in != out, butterfly-path
+ * plans, no overlap).  n == 0 launches nothing.
+ * d_status: device pointer to one uint32_t (4-byte aligned), set to 0 at the
  * start of the call and to NTT_ERR_TIMEOUT if a device wait of the kernel
- * ran out; may be NULL.
+ * ran out.  It may be NULL: the error is then kept in the array's own error
+ * word until ntt_batch_poll_error reads and clears it, and until then later
+ * calls made without a status pointer stop at once (like ntt_batch_submit
+ * after an unpolled error).
  *
- * The first call on a device looks up the array's device address once
- * (cudaGetSymbolAddress).  Every call on a device shares the one array,
- * which keeps the
- * last call's contents (the call clears the counters it needs): calls whose
- * work overlaps on the GPU race -- order them on one stream.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, which may load the library's device code on that
+ * device); make that first call before any stream capture.  The address is
+ * kept until ntt_batch_cache_clear, which must be called after a
+ * cudaDeviceReset.  Every call on a device shares the one array, which keeps
+ * the last call's contents (the call clears the counters it needs): calls
+ * whose work overlaps on the GPU race -- order them on one stream.
  */
 ntt_status ntt_batch_submit_static(const ntt_job *jobs, size_t n, uint32_t *d_status, ntt_stream stream);
 
 /* First error recorded by batched kernels on the current device since the
- * last poll (0 = none), then cleared.  Synchronises the device. */
+ * last poll (0 = none), then cleared: ntt_batch_submit's word, else the word
+ * of ntt_batch_submit_static calls made without a status pointer.
+ * Synchronises the device. */
 ntt_status ntt_batch_poll_error(uint32_t *code);
 
 /* Bound of every device-side wait of batches built from now on (ns, > 0).
@@ -288,19 +315,21 @@ ntt_status ntt_batch_set_wait_limit(uint64_t ns);
  * is involved.  Drops the cached job lists. */
 ntt_status ntt_batch_debug_stall(int enable);
 
-/* Drop every cached job list (synchronises the device). */
+/* Drop every cached job list (synchronises the device) and forget the
+ * device addresses looked up by ntt_batch_submit_static. */
 ntt_status ntt_batch_cache_clear(void);
 
 /*
  * Per-pass launch timing.  While enabled, every pass launch of this plan's
  * transforms is bracketed by two CUDA events recorded on the launch's own
  * stream.  ntt_plan_read_timing synchronises those events and returns, per
- * pass (up to 4), the summed device time in milliseconds and the number of
- * launches timed since the last read, then clears the record.  Timing adds
+ * pass (up to NTT_MAX_PASSES), the summed device time in milliseconds and
+ * the number of launches timed since the last read, then clears the record.  Timing adds
  * two event records per launch; leave it off outside measurements.
  */
 ntt_status ntt_plan_enable_timing(ntt_plan plan, int enable);
-ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[4], uint64_t launches_per_pass[4]);
+ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[NTT_MAX_PASSES],
+                                uint64_t launches_per_pass[NTT_MAX_PASSES]);
 
 /*
  * Device-detected error of the plan's last transforms (0 = none), cleared on

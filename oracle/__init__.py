@@ -55,12 +55,15 @@ KIND = {"forward": 0, "inverse": 1, "coset": 2, "coset_inverse": 3}
 
 
 def build_c_oracle(force: bool = False) -> str:
-    """Compile the C oracle with gcc (plain -O2, no -march, portable to Arm)."""
+    """Compile the C oracle with gcc (plain -O2, no -march, portable to Arm;
+    OpenMP for its optional all-cores mode, without it if gcc lacks it)."""
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC], check=True)
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC]
+    if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+        subprocess.run(base, check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -80,8 +83,16 @@ def c_oracle():
             lib.oracle_root.restype = ctypes.c_int
             lib.oracle_mul.argtypes = [ctypes.c_int, u64p, u64p, u64p]
             lib.oracle_mul.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
+
+
+def c_set_threads(k: int) -> int:
+    """Threads of the C oracle's butterfly stages from now on (1 = serial,
+    0 = all cores); returns the count in use (1 without OpenMP)."""
+    return int(c_oracle().oracle_set_threads(int(k)))
 
 
 def _ptr(a: np.ndarray):

@@ -16,11 +16,21 @@
  * multiplicative generator.  Elements are canonical, natural order,
  * 4 little-endian uint64 limbs each.
  *
- * Single-threaded on purpose: it is the reported CPU baseline "as it stands".
+ * Single-threaded by default: it is the reported CPU baseline "as it
+ * stands".  oracle_set_threads(k) with k > 1 splits the butterflies of each
+ * stage over k OpenMP threads (each thread takes a run of consecutive
+ * butterflies and starts its twiddle at w^j by exponentiation); the
+ * arithmetic and the results are the same.  That mode is the all-cores CPU
+ * baseline.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int n_threads = 1;
 
 typedef unsigned __int128 u128;
 
@@ -185,6 +195,32 @@ static void inv_mont(const field_t *F, const uint64_t a_mont[4], uint64_t r[4]) 
     mont_pow(F, r, a_mont, e);
 }
 
+/* One radix-2 stage (butterfly span len, twiddle root wl) with the n/2
+ * butterflies t = block * len/2 + j split into runs over the threads; a run
+ * starts its twiddle at wl^j (exponentiation) and steps it like the serial
+ * loop, restarting at 1 where a new block begins. */
+static void stage_threaded(const field_t *F, uint64_t (*a)[4], uint64_t n, uint64_t len, const uint64_t wl[4]) {
+    const uint64_t half = len >> 1, total = n >> 1;
+    const int64_t runs = (int64_t)(total < 4096 ? 1 : 4 * (uint64_t)n_threads);
+#pragma omp parallel for schedule(static) num_threads(n_threads)
+    for (int64_t r = 0; r < runs; r++) {
+        const uint64_t t0 = total * (uint64_t)r / (uint64_t)runs, t1 = total * (uint64_t)(r + 1) / (uint64_t)runs;
+        uint64_t wj[4];
+        uint64_t e[4] = {t0 % half, 0, 0, 0};
+        mont_pow(F, wj, wl, e);
+        for (uint64_t t = t0; t < t1; t++) {
+            const uint64_t j = t % half, i0 = (t / half) * len + j;
+            if (j == 0) memcpy(wj, F->r1, sizeof wj);
+            uint64_t u[4], v[4];
+            memcpy(u, a[i0], sizeof u);
+            mont_mul(F, v, a[i0 + half], wj);
+            add_mod(F, a[i0], u, v);
+            sub_mod(F, a[i0 + half], u, v);
+            mont_mul(F, wj, wj, wl);
+        }
+    }
+}
+
 /* In-place iterative radix-2 DIT on Montgomery-form data with root w. */
 static void radix2(const field_t *F, uint64_t (*a)[4], uint64_t n, unsigned log_n, const uint64_t w[4]) {
     for (uint64_t i = 0; i < n; i++) {
@@ -203,6 +239,10 @@ static void radix2(const field_t *F, uint64_t (*a)[4], uint64_t n, unsigned log_
         /* w_len = w^(n/len): square w (log_n - s) times. */
         memcpy(wl, w, sizeof wl);
         for (unsigned k = s; k < log_n; k++) mont_mul(F, wl, wl, wl);
+        if (n_threads > 1) {
+            stage_threaded(F, a, n, len, wl);
+            continue;
+        }
         for (uint64_t start = 0; start < n; start += len) {
             uint64_t wj[4];
             memcpy(wj, F->r1, sizeof wj);
@@ -318,4 +358,17 @@ int oracle_mul(int field, const uint64_t *a, const uint64_t *b, uint64_t *out) {
     to_mont(F, am, a);
     mont_mul(F, out, am, b);
     return 0;
+}
+
+/* Threads for the butterfly stages of later oracle_ntt calls (1 = the plain
+ * serial loop; 0 = every core OpenMP sees).  Returns the count now in use. */
+int oracle_set_threads(int k) {
+#ifdef _OPENMP
+    if (k <= 0) k = omp_get_num_procs();
+    n_threads = k;
+#else
+    (void)k;
+    n_threads = 1;
+#endif
+    return n_threads;
 }

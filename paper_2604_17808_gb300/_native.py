@@ -27,6 +27,7 @@ PATH = {"auto": 0, "butterfly": 1, "matrix": 2}
 HEADER = os.path.join(_build.ROOT, "include", "ntt_gb300.h")
 HEADERS = (HEADER, os.path.join(_build.ROOT, "include", "msm_gb300.h"))
 CURVE = {"bn254_g1": 0, "bls12_381_g1": 1}
+MAX_PASSES = 12  # NTT_MAX_PASSES
 
 
 class NttError(RuntimeError):
@@ -38,7 +39,7 @@ class NttError(RuntimeError):
 class PlanDesc(ctypes.Structure):
     _fields_ = [
         ("field", ctypes.c_uint32), ("log_n", ctypes.c_uint32), ("num_passes", ctypes.c_uint32),
-        ("pass_log", ctypes.c_uint32 * 4), ("launches_per_transform", ctypes.c_uint32),
+        ("pass_log", ctypes.c_uint32 * MAX_PASSES), ("launches_per_transform", ctypes.c_uint32),
         ("path", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
     ]
 
@@ -56,8 +57,9 @@ class ServerStats(ctypes.Structure):
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("path", ctypes.c_uint32), ("num_passes", ctypes.c_uint32), ("pass_log", ctypes.c_uint32 * 4),
-                ("tile_log", ctypes.c_uint32 * 4), ("candidates", ctypes.c_uint32), ("best_ms", ctypes.c_double),
+    _fields_ = [("path", ctypes.c_uint32), ("num_passes", ctypes.c_uint32),
+                ("pass_log", ctypes.c_uint32 * MAX_PASSES), ("tile_log", ctypes.c_uint32 * MAX_PASSES),
+                ("candidates", ctypes.c_uint32), ("best_ms", ctypes.c_double),
                 ("default_ms", ctypes.c_double)]
 
 
@@ -93,6 +95,7 @@ _SIGS = {
     "ntt_plan_read_table": (ctypes.c_int, [_VP, ctypes.c_int, _U32, _U32, _U64, _U64, _VP]),
     "ntt_batch_submit": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP]),
     "ntt_plan_autotune": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(TuneResult)]),
+    "ntt_plan_set_passes": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_U32), _U32]),
     "ntt_plan_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
     "ntt_batch_submit_static": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP, _VP]),
     "ntt_batch_poll_error": (ctypes.c_int, [ctypes.POINTER(_U32)]),
@@ -270,8 +273,14 @@ def ntt_plan_autotune(plan: int, reps: int = 3) -> dict:
     _check(load().ntt_plan_autotune(plan, int(reps), ctypes.byref(r)), "ntt_plan_autotune")
     n = r.num_passes
     return {"path": ["auto", "butterfly", "matrix"][r.path], "num_passes": n,
-            "pass_log": list(r.pass_log)[: min(n, 4)], "tile_log": list(r.tile_log)[: min(n, 4)],
+            "pass_log": list(r.pass_log)[:n], "tile_log": list(r.tile_log)[:n],
             "candidates": r.candidates, "best_ms": r.best_ms, "default_ms": r.default_ms}
+
+
+def ntt_plan_set_passes(plan: int, pass_log: list[int], tile_log: int = 10) -> None:
+    """Rebuild the plan's butterfly path for an explicit pass split."""
+    arr = (_U32 * len(pass_log))(*pass_log)
+    _check(load().ntt_plan_set_passes(plan, len(pass_log), arr, int(tile_log)), "ntt_plan_set_passes")
 
 
 def ntt_batch_submit(jobs, stream=None) -> None:
@@ -372,8 +381,8 @@ def ntt_plan_enable_timing(plan: int, enable: bool = True) -> None:
 
 def ntt_plan_read_timing(plan: int) -> tuple[list[float], list[int]]:
     """(summed ms per pass, launches per pass) since the last read."""
-    ms = (ctypes.c_double * 4)()
-    cnt = (_U64 * 4)()
+    ms = (ctypes.c_double * MAX_PASSES)()
+    cnt = (_U64 * MAX_PASSES)()
     _check(load().ntt_plan_read_timing(plan, ms, cnt), "ntt_plan_read_timing")
     return list(ms), list(cnt)
 

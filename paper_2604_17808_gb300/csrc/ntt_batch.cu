@@ -135,6 +135,11 @@ std::vector<BatchSeg> build_segments(const std::vector<BatchJobRef> &jobs, int f
 
 uint64_t batch_wait_limit_ns() { return g_wait_ns; }
 
+bool batch_debug_stall() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_stall;
+}
+
 ntt_status batch_error_word(uint32_t **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_NO_DEVICE;
@@ -269,6 +274,10 @@ ntt_status ntt_batch_poll_error(uint32_t *code) {
   if (s != NTT_OK) return s;
   s = cuda_status(cudaMemcpy(code, err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   if (s == NTT_OK) s = cuda_status(cudaMemset(err, 0, sizeof(uint32_t)));
+  // the word of allocation-free calls made without a status pointer
+  uint32_t scode = 0;
+  if (s == NTT_OK) s = static_batch_take_error(dev, &scode);
+  if (s == NTT_OK && !*code) *code = scode;
   return s;
 }
 
@@ -290,6 +299,7 @@ ntt_status ntt_batch_debug_stall(int enable) {
 ntt_status ntt_batch_cache_clear(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   clear_cache_locked();
+  static_batch_forget_addresses();
   return NTT_OK;
 }
 

@@ -23,12 +23,16 @@ using namespace gb300ntt;
 namespace {
 
 constexpr uint32_t kStaticMaxJobs = 64;
-constexpr uint32_t kStaticMaxSegs = kStaticMaxJobs * 4;  // per field (a job has at most 4 passes)
+// Segments (passes of jobs) per field per call: four per job on average.
+// A job has at most kMaxPasses passes; a call whose jobs need more than
+// kStaticMaxSegs segments in one field is rejected (NTT_ERR_UNSUPPORTED).
+constexpr uint32_t kStaticMaxSegs = kStaticMaxJobs * 4;
 
 struct StaticScratch {
   BatchSeg segs[2][kStaticMaxSegs];       // work-item tables, one per field
   uint32_t ctl[2][1 + kStaticMaxSegs];    // [0] = next item, [1 + s] = tiles done of segment s
   uint32_t err;                           // error word when the caller passes no status
+                                          // (read and cleared by ntt_batch_poll_error)
 };
 
 // Work-item table of the jobs of one field into `out` (capacity
@@ -37,7 +41,7 @@ struct StaticScratch {
 ntt_status static_segments(const ntt_job *jobs, size_t n, int field, BatchSeg *out, uint32_t *count,
                            uint32_t *total_items) {
   uint32_t order[kStaticMaxJobs];
-  int seg_of[kStaticMaxJobs][4];
+  int seg_of[kStaticMaxJobs][kMaxPasses];  // [job][pass] -> segment index
   uint32_t m = 0, max_passes = 0;
   for (size_t i = 0; i < n; ++i) {
     if (jobs[i].plan->field != field) continue;
@@ -67,6 +71,15 @@ ntt_status static_segments(const ntt_job *jobs, size_t n, int field, BatchSeg *o
       ++segs;
     }
   }
+  if (batch_debug_stall()) {
+    // test hook (as in ntt_batch_submit): the last segment with a dependency
+    // waits for one tile more than exists, so its bounded wait runs out
+    for (int k = (int)segs - 1; k >= 0; --k)
+      if (out[k].dep_seg >= 0) {
+        out[k].dep_tiles += 1;
+        break;
+      }
+  }
   *count = segs;
   *total_items = item;
   return NTT_OK;
@@ -84,7 +97,9 @@ std::mutex g_static_mu;
 StaticScratch *g_static_addr[64] = {};  // device address of g_static_scratch, per device
 
 // Once per device, with that device current: the device address of the
-// array (its name in host code is only a host-side stand-in).
+// array (its name in host code is only a host-side stand-in).  The address
+// is kept until ntt_batch_cache_clear (after a cudaDeviceReset the module
+// is loaded anew and the address must be looked up again).
 ntt_status static_scratch_address(int dev, StaticScratch **out) {
   if (dev < 0 || dev >= 64) return NTT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_static_mu);
@@ -99,6 +114,31 @@ ntt_status static_scratch_address(int dev, StaticScratch **out) {
 }
 
 }  // namespace
+
+namespace gb300ntt {
+
+// The error word of calls made without a status pointer, read and cleared
+// for ntt_batch_poll_error (0 when this device never ran such a call).
+ntt_status static_batch_take_error(int dev, uint32_t *code) {
+  *code = 0;
+  if (dev < 0 || dev >= 64) return NTT_ERR_INVALID_ARG;
+  StaticScratch *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    scratch = g_static_addr[dev];
+  }
+  if (!scratch) return NTT_OK;
+  ntt_status s = cuda_status(cudaMemcpy(code, &scratch->err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (s == NTT_OK && *code) s = cuda_status(cudaMemset(&scratch->err, 0, sizeof(uint32_t)));
+  return s;
+}
+
+void static_batch_forget_addresses() {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  for (StaticScratch *&a : g_static_addr) a = nullptr;
+}
+
+}  // namespace gb300ntt
 
 extern "C" ntt_status ntt_batch_submit_static(const ntt_job *jobs, size_t n, uint32_t *d_status, ntt_stream stream) {
   if (!jobs && n) return NTT_ERR_INVALID_ARG;
@@ -119,8 +159,11 @@ extern "C" ntt_status ntt_batch_submit_static(const ntt_job *jobs, size_t n, uin
   ntt_status st = static_scratch_address(dev, &scratch);
   if (st != NTT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  // With a status pointer the call reports into it (cleared first); without
+  // one, into the array's error word, which keeps the first error until
+  // ntt_batch_poll_error reads it (as the word of ntt_batch_submit does).
   uint32_t *err = d_status ? d_status : &scratch->err;
-  if (cudaMemsetAsync(err, 0, sizeof(uint32_t), s) != cudaSuccess) return NTT_ERR_CUDA;
+  if (d_status && cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return NTT_ERR_CUDA;
   if (n == 0) return NTT_OK;
   BatchSeg host_segs[kStaticMaxSegs];
   for (int field = 0; field < 2; ++field) {

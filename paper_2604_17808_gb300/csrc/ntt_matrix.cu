@@ -170,7 +170,7 @@ ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *
     ma.wait_ns = 1000000000ull;
     const uint64_t tiles = (ma.a.num_sub + kMatRows - 1) / kMatRows;
     const uint32_t grid = (uint32_t)(tiles < (uint64_t)p->sm_count ? tiles : (uint64_t)p->sm_count);
-    cudaError_t e = timing_begin(p, (int)(j < 4 ? j : 3), st);
+    cudaError_t e = timing_begin(p, (int)j, st);
     if (e == cudaSuccess) e = L.matrix_pass((int)logs, mode, ma, grid, st);
     if (e == cudaSuccess) e = timing_end(p, st);
     if (e != cudaSuccess) return cuda_status(e);

@@ -83,8 +83,8 @@ enum PassMode : int {
   kModeFirstPre = 2,  // pass 0 with a per-n_0 input multiplier table [S]
 };
 
-// At most this many passes per transform (the matrix path splits 2^28 into
-// ten passes of at most 2^3 points).
+// At most this many passes per transform (NTT_MAX_PASSES of the C ABI: the
+// matrix path splits 2^28 into ten passes of at most 2^3 points).
 constexpr int kMaxPasses = 12;
 
 struct PassArgs {

@@ -469,7 +469,7 @@ ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out) {
   out->field = (uint32_t)plan->field;
   out->log_n = plan->log_n;
   out->num_passes = plan->num_passes;
-  for (uint32_t j = 0; j < plan->num_passes && j < 4; ++j) out->pass_log[j] = plan->pass_log[j];
+  for (uint32_t j = 0; j < plan->num_passes && j < NTT_MAX_PASSES; ++j) out->pass_log[j] = plan->pass_log[j];
   out->launches_per_transform = plan->path == NTT_PATH_MATRIX ? matrix_launches(plan) : plan->launches;
   out->path = (uint32_t)plan->path;
   out->device_bytes = plan->device_bytes;
@@ -523,9 +523,10 @@ ntt_status ntt_plan_enable_timing(ntt_plan plan, int enable) {
   return NTT_OK;
 }
 
-ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[4], uint64_t launches_per_pass[4]) {
+ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[NTT_MAX_PASSES],
+                                uint64_t launches_per_pass[NTT_MAX_PASSES]) {
   if (!plan || !ms_per_pass || !launches_per_pass) return NTT_ERR_INVALID_ARG;
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < NTT_MAX_PASSES; ++j) {
     ms_per_pass[j] = 0;
     launches_per_pass[j] = 0;
   }
@@ -534,7 +535,7 @@ ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[4], uint64_t l
     float ms = 0;
     const cudaError_t e = cudaEventSynchronize(u.second.second);
     if (e == cudaSuccess && cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess) {
-      if (u.first >= 0 && u.first < 4) {
+      if (u.first >= 0 && u.first < NTT_MAX_PASSES) {
         ms_per_pass[u.first] += ms;
         launches_per_pass[u.first] += 1;
       }

@@ -117,6 +117,10 @@ struct BatchJobRef {
 };
 std::vector<BatchSeg> build_segments(const std::vector<BatchJobRef> &jobs, int field, uint32_t *total_items);
 uint64_t batch_wait_limit_ns();
+bool batch_debug_stall();  // the ntt_batch_debug_stall test hook is on
 ntt_status batch_error_word(uint32_t **out);
+// allocation-free batch (ntt_batch_static.cu)
+ntt_status static_batch_take_error(int dev, uint32_t *code);
+void static_batch_forget_addresses();
 
 }  // namespace gb300ntt

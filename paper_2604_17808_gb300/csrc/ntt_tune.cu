@@ -225,7 +225,7 @@ extern "C" ntt_status ntt_plan_autotune(ntt_plan plan, uint32_t reps, ntt_tune_r
     std::memset(result, 0, sizeof *result);
     result->path = (uint32_t)plan->path;
     result->num_passes = plan->num_passes;
-    for (uint32_t j = 0; j < plan->num_passes && j < 4; ++j) {
+    for (uint32_t j = 0; j < plan->num_passes && j < NTT_MAX_PASSES; ++j) {
       result->pass_log[j] = plan->pass_log[j];
       result->tile_log[j] = plan->pass_tl[j];
     }
@@ -233,5 +233,26 @@ extern "C" ntt_status ntt_plan_autotune(ntt_plan plan, uint32_t reps, ntt_tune_r
     result->default_ms = default_ms;
     result->candidates = tried;
   }
+  return s;
+}
+
+extern "C" ntt_status ntt_plan_set_passes(ntt_plan plan, uint32_t num_passes, const uint32_t *pass_log,
+                                          uint32_t tile_log) {
+  if (!plan || !pass_log) return NTT_ERR_INVALID_ARG;
+  if (num_passes < 1 || num_passes > (uint32_t)kMaxPasses) return NTT_ERR_INVALID_ARG;
+  if (tile_log != 10 && tile_log != 11) return NTT_ERR_INVALID_ARG;
+  std::vector<uint32_t> split(pass_log, pass_log + num_passes);
+  uint32_t sum = 0;
+  for (uint32_t s : split) {
+    if (s < 1 || s > (uint32_t)kMaxPassLog) return NTT_ERR_INVALID_ARG;
+    sum += s;
+  }
+  if (sum != plan->log_n) return NTT_ERR_INVALID_ARG;
+  cudaStream_t st = nullptr;
+  ntt_status s = cuda_status(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  if (s != NTT_OK) return s;
+  s = apply_butterfly(plan, split, tile_log, st);
+  cudaStreamDestroy(st);
+  if (s == NTT_OK) plan->path = NTT_PATH_BUTTERFLY;
   return s;
 }

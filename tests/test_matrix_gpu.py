@@ -128,6 +128,28 @@ def test_matrix_path_bn254_2_24_coset_matches_oracle_digest():
     assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == want["output_sha256"]
 
 
+@pytest.mark.parametrize("kind", ["forward", "inverse"])
+def test_matrix_path_bls12_381_2_24_matches_oracle_digest(kind):
+    # the 2^24-point BLS12-381 transform on the tensor-core path, whole output
+    # against the stored oracle digest
+    field, log_n = "bls12_381_fr", 24
+    x = uniform_elements(field, 1 << log_n, config_seed(3, 100))
+    with open(os.path.join(HERE, "golden", "oracle_digests.json")) as fh:
+        want = [c for c in json.load(fh)["single"]
+                if c["config"] == 3 and c["kind"] == kind and c["field"] == field][0]
+    assert hashlib.sha256(x.astype("<u8").tobytes()).hexdigest() == want["input_sha256"]
+    plan = matrix_plan(field, log_n, coset=False)
+    try:
+        d_x = dev(x)
+        d_y = torch.empty_like(d_x)
+        N.ntt_execute(plan, kind, d_x, d_y)
+        got = host(d_y)
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+    assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == want["output_sha256"]
+
+
 def test_matrix_path_in_place_and_custom_shift():
     field, log_n = "bn254_fr", 13
     f = O.get_field(field)

@@ -233,11 +233,11 @@ def test_device_twiddle_tables_match_oracle_roots(field):
 # ------------------------------------------------------- workload sizes
 
 
-def _golden_case(config, kind):
+def _golden_case(config, kind, field=None):
     for c in golden()["single"]:
-        if c["config"] == config and c["kind"] == kind:
+        if c["config"] == config and c["kind"] == kind and (field is None or c["field"] == field):
             return c
-    raise KeyError((config, kind))
+    raise KeyError((config, kind, field))
 
 
 @pytest.mark.parametrize("kind", ["forward", "inverse"])
@@ -292,9 +292,15 @@ def test_bn254_2_24_coset_matches_digest_and_sampled_outputs():
     _horner_spot_checks(field, x, got, "coset", samples=2, seed=3)
 
 
-def test_bls12_381_2_24_forward_sampled_outputs_and_round_trip():
+def test_bls12_381_2_24_forward_and_inverse_match_oracle_digests():
+    """The 2^24-point BLS12-381 transform, compared in full: forward and
+    inverse outputs against the stored C-oracle digests, the round trip, and
+    sampled outputs evaluated one by one (Horner at omega^k)."""
     field, log_n = "bls12_381_fr", 24
     x = uniform_elements(field, 1 << log_n, config_seed(3, 100))
+    gf = _golden_case(3, "forward", field)
+    gi = _golden_case(3, "inverse", field)
+    assert digest(x) == gf["input_sha256"] == gi["input_sha256"]
     plan = N.ntt_plan_create(field, log_n)
     try:
         d_x = dev(x)
@@ -304,14 +310,20 @@ def test_bls12_381_2_24_forward_sampled_outputs_and_round_trip():
         N.ntt_inverse(plan, d_y, d_z)
         y = host(d_y)
         assert torch.equal(d_z, d_x)
+        N.ntt_inverse(plan, d_x, d_z)
+        z = host(d_z)
     finally:
         N.ntt_plan_destroy(plan)
+    assert digest(y) == gf["output_sha256"]
+    assert digest(z) == gi["output_sha256"]
     _horner_spot_checks(field, x, y, "forward", samples=2, seed=4)
 
 
 def test_maximum_size_2_28_round_trip_and_sampled_outputs():
     # 2^28 points (BN254 Fr's 2-adicity, the largest size the library takes):
-    # 8 GiB per vector.  The oracle evaluates sampled outputs one by one.
+    # 8 GiB per vector.  Checked by the round trip and by sampled outputs the
+    # oracle evaluates one by one (a full oracle transform of this size takes
+    # minutes on one core and is not stored).
     field, log_n = "bn254_fr", 28
     n = 1 << log_n
     x = uniform_elements(field, n, 0x5EED0100)

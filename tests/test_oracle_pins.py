@@ -463,3 +463,23 @@ def test_planted_mistake_is_caught(name):
     field = O.BN254_FR
     failed = [p.__name__ for p in ALL_PINS if not p(impl, field)]
     assert failed, f"no pin caught the planted mistake {name}"
+
+
+def test_c_oracle_all_cores_mode_equals_serial():
+    """The C oracle's OpenMP mode (the all-cores CPU baseline) splits each
+    stage's butterflies into runs that start their twiddle by exponentiation;
+    it must give the serial loop's bytes for every kind and size, including
+    sizes whose stages have fewer butterflies than runs."""
+    from ntt_synth import uniform_elements
+
+    try:
+        for field in ("bls12_381_fr", "bn254_fr"):
+            for log_n in (1, 3, 12, 14):
+                x = uniform_elements(field, 1 << log_n, 7700 + log_n)
+                for kind in ("forward", "inverse", "coset", "coset_inverse"):
+                    oracle.c_set_threads(1)
+                    serial = oracle.c_transform(field, kind, x)
+                    oracle.c_set_threads(4)
+                    assert np.array_equal(oracle.c_transform(field, kind, x), serial), (field, log_n, kind)
+    finally:
+        oracle.c_set_threads(1)

@@ -72,3 +72,41 @@ def test_autotune_keeps_results_exact_and_remembers_the_choice(tmp_path, monkeyp
         assert np.array_equal(host(d_y), oracle.c_transform(field, "forward", x))
     finally:
         N.ntt_plan_destroy(plan2)
+
+
+@pytest.mark.parametrize("field,log_n,split,tile", [
+    ("bls12_381_fr", 13, [13 - 11, 11], 11), ("bn254_fr", 16, [4, 4, 4, 4], 10),
+    ("bls12_381_fr", 17, [1, 5, 11], 10), ("bn254_fr", 15, [3, 3, 3, 3, 3], 11),
+    ("bls12_381_fr", 11, [11], 11), ("bn254_fr", 12, [1] * 12, 10)])
+def test_explicit_pass_split_is_exact(field, log_n, split, tile):
+    """ntt_plan_set_passes: any split (here up to NTT_MAX_PASSES passes, either
+    tile shape) gives the same, exact transform for all four kinds."""
+    N.load(build_if_missing=True)
+    x = uniform_elements(field, 1 << log_n, 60100 + log_n)
+    plan = N.ntt_plan_create(field, log_n, coset=True)
+    try:
+        N.ntt_plan_set_passes(plan, split, tile)
+        d = N.ntt_plan_describe(plan)
+        assert d["pass_log"] == split and d["launches_per_transform"] == len(split)
+        for kind in ("forward", "inverse", "coset", "coset_inverse"):
+            d_x = dev(x)
+            d_y = torch.empty_like(d_x)
+            N.ntt_execute(plan, kind, d_x, d_y)
+            assert np.array_equal(host(d_y), oracle.c_transform(field, kind, x)), kind
+        # in place (the plan's scratch carries the passes before the last)
+        d_x = dev(x)
+        N.ntt_execute(plan, "forward", d_x, d_x)
+        assert np.array_equal(host(d_x), oracle.c_transform(field, "forward", x))
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
+def test_explicit_pass_split_rejects_bad_splits():
+    N.load(build_if_missing=True)
+    plan = N.ntt_plan_create("bls12_381_fr", 14)
+    try:
+        for split, tile in (([7, 6], 10), ([12, 2], 11), ([7, 7], 9), ([1] * 14, 10), ([], 10)):
+            with pytest.raises(N.NttError):
+                N.ntt_plan_set_passes(plan, split, tile)
+    finally:
+        N.ntt_plan_destroy(plan)
