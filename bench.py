@@ -298,9 +298,27 @@ def measure_2_24(torch, N, stream, steps: int) -> dict:
             mm = pass_modmuls(log_n, desc["pass_log"], j, j >= 1)
             per_pass.append({"pass": j, "log_s": ls, "avg_ms": round(avg, 4),
                              "frac": round(mm * IMAD_PER_MODMUL / (avg * 1e-3) / 1e12 / peak, 4)})
+        # the same transform on the matrix (tensor-core) path, outputs compared
+        N.ntt_plan_set_path(plan, "matrix")
+        ym = torch.empty_like(ys[0])
+        N.ntt_forward(plan, xs[0], ym, stream)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for i in range(steps):
+            N.ntt_forward(plan, xs[i % 2], ym if i % 2 == 0 else ys[1], stream)
+        stop.record(stream)
+        stop.synchronize()
+        ms_m = start.elapsed_time(stop) / steps
+        N.ntt_forward(plan, xs[0], ym, stream)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(ym, ys[0]))
+        mdesc = N.ntt_plan_describe(plan)
         return {"workload": "BLS12-381 Fr forward NTT, n=2^24, butterfly path", "ms": round(ms, 4),
                 "elements_per_s": (1 << log_n) / (ms * 1e-3),
-                "imad_roofline_frac": round(alg / (ms * 1e-3) / 1e12 / peak, 4), "passes": per_pass}
+                "imad_roofline_frac": round(alg / (ms * 1e-3) / 1e12 / peak, 4), "passes": per_pass,
+                "matrix_path": {"ms": round(ms_m, 4), "elements_per_s": (1 << log_n) / (ms_m * 1e-3),
+                                "passes": mdesc["launches_per_transform"], "identical_to_butterfly": same,
+                                "device_error": N.ntt_plan_poll_error(plan)}}
     finally:
         N.ntt_plan_destroy(plan)
 

@@ -240,8 +240,8 @@ ntt_status ntt_plan_set_passes(ntt_plan plan, uint32_t num_passes, const uint32_
  * jobs[i].plan fixes field and size; kind is an ntt_kind; in/out are device
  * buffers as above.  Jobs must not overlap in memory, and in != out for every
  * job (in-place jobs are rejected with NTT_ERR_INVALID_ARG: the batched path
- * works in the output buffer).  Plans on the matrix path are rejected with
- * NTT_ERR_UNSUPPORTED.
+ * works in the output buffer).  Jobs whose plan is on the matrix path run as
+ * ordinary transforms inside the same graph (see ntt_batch_autotune).
  *
  * The first submission of a given job list (same plans, kinds and pointers)
  * builds its work-item table on the device and captures the launch sequence
@@ -262,6 +262,32 @@ typedef struct ntt_job {
     void *out;
 } ntt_job;
 ntt_status ntt_batch_submit(const ntt_job *jobs, size_t n, ntt_stream stream);
+
+/*
+ * Autotuner of a job list (the batch-size ablation of Sec. 4.4 / Fig. 7 asks
+ * how batching should be organised; here it is measured per job list).
+ * Candidates: every job in the persistent kernel; or, for each distinct job
+ * size 2^t of the list, the jobs of 2^t points and more taken out of it and
+ * run as ordinary transforms (each on its plan's own path and pass split,
+ * e.g. as chosen by ntt_plan_autotune) over 1, 2 or 4 parallel branches of
+ * the same CUDA graph, concurrently with the persistent kernel for the rest.
+ * Each candidate runs the list once untimed and `reps` times timed (reps = 0:
+ * 3), so the output buffers end up holding the jobs' results.  The fastest
+ * policy is kept for the list's signature (the multiset of field, size,
+ * kind and path of its jobs): later ntt_batch_submit calls of any list with
+ * that signature follow it, and with NTT_TUNE_CACHE set the policies are
+ * also written to "<NTT_TUNE_CACHE>.batch" and read by later processes.
+ * Synchronous.  result may be NULL.
+ */
+typedef struct ntt_batch_tune_result {
+    uint32_t split_log;      /* jobs of 2^split_log points and more run alone (0: none) */
+    uint32_t branches;       /* parallel graph branches for them (0: none) */
+    uint32_t candidates;
+    double best_ms;          /* the list under the chosen policy */
+    double persistent_ms;    /* every job in the persistent kernel */
+    double loop_ms;          /* one ntt_execute per job on one stream */
+} ntt_batch_tune_result;
+ntt_status ntt_batch_autotune(const ntt_job *jobs, size_t n, uint32_t reps, ntt_batch_tune_result *result);
 
 /*
  * ntt_batch_submit without any allocation.  The paper has no counterpart:
@@ -315,8 +341,10 @@ ntt_status ntt_batch_set_wait_limit(uint64_t ns);
  * is involved.  Drops the cached job lists. */
 ntt_status ntt_batch_debug_stall(int enable);
 
-/* Drop every cached job list (synchronises the device) and forget the
- * device addresses looked up by ntt_batch_submit_static. */
+/* Drop every cached job list (synchronises the device), the batch policies
+ * of ntt_batch_autotune held in memory (those in "<NTT_TUNE_CACHE>.batch"
+ * are read again) and the device addresses looked up by
+ * ntt_batch_submit_static. */
 ntt_status ntt_batch_cache_clear(void);
 
 /*

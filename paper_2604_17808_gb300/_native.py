@@ -63,6 +63,11 @@ class TuneResult(ctypes.Structure):
                 ("default_ms", ctypes.c_double)]
 
 
+class BatchTuneResult(ctypes.Structure):
+    _fields_ = [("split_log", ctypes.c_uint32), ("branches", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
+                ("best_ms", ctypes.c_double), ("persistent_ms", ctypes.c_double), ("loop_ms", ctypes.c_double)]
+
+
 class MsmPlanDesc(ctypes.Structure):
     _fields_ = [("max_n", ctypes.c_uint64), ("window_bits", ctypes.c_uint32), ("num_windows", ctypes.c_uint32),
                 ("segment_length", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
@@ -94,6 +99,7 @@ _SIGS = {
     "ntt_plan_describe": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc)]),
     "ntt_plan_read_table": (ctypes.c_int, [_VP, ctypes.c_int, _U32, _U32, _U64, _U64, _VP]),
     "ntt_batch_submit": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP]),
+    "ntt_batch_autotune": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _U32, ctypes.POINTER(BatchTuneResult)]),
     "ntt_plan_autotune": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(TuneResult)]),
     "ntt_plan_set_passes": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_U32), _U32]),
     "ntt_plan_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
@@ -290,6 +296,18 @@ def ntt_batch_submit(jobs, stream=None) -> None:
     for i, (plan, kind, d_in, d_out) in enumerate(jobs):
         arr[i] = Job(plan, _kind(kind), _ptr(d_in), _ptr(d_out))
     _check(load().ntt_batch_submit(arr, len(jobs), _stream(stream)), "ntt_batch_submit")
+
+
+def ntt_batch_autotune(jobs, reps: int = 3) -> dict:
+    """jobs: iterable of (plan, kind, d_in, d_out); returns the chosen policy and its timings."""
+    jobs = list(jobs)
+    arr = (Job * max(1, len(jobs)))()
+    for i, (plan, kind, x, y) in enumerate(jobs):
+        arr[i] = Job(plan, _kind(kind), _ptr(x), _ptr(y))
+    r = BatchTuneResult()
+    _check(load().ntt_batch_autotune(arr, len(jobs), int(reps), ctypes.byref(r)), "ntt_batch_autotune")
+    return {"split_log": r.split_log, "branches": r.branches, "candidates": r.candidates, "best_ms": r.best_ms,
+            "persistent_ms": r.persistent_ms, "loop_ms": r.loop_ms}
 
 
 def ntt_batch_submit_static(jobs, d_status=None, stream=None) -> None:

@@ -1,5 +1,5 @@
-// BLS12-381 scalar field: table generators, element-wise kernels, the matrix-form
-// pass and the field's launcher table.
+// BLS12-381 scalar field: table generators, element-wise kernels and the field's
+// launcher table.
 #define NTT_FIELD FieldBls12381Fr
 #define NTT_NS bls12_381
 #define NTT_PART_MISC

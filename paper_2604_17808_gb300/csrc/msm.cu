@@ -64,6 +64,7 @@
 
 #include "../../include/msm_gb300.h"
 #include "ec_xyzz.cuh"
+#include "nvtx_range.h"
 
 namespace gb300ntt {
 namespace {
@@ -1107,6 +1108,7 @@ ntt_status msm_plan_destroy(msm_plan plan) {
 
 ntt_status msm_execute(msm_plan p, const void *d_scalars, const void *d_points, uint64_t n, void *d_result,
                        ntt_stream stream) {
+  gb300ntt::NvtxRange range("msm_execute");
   if (!p || !d_result || ((uintptr_t)d_result % 16)) return NTT_ERR_INVALID_ARG;
   if (n > p->max_n) return NTT_ERR_INVALID_ARG;
   const uintptr_t pa = p->curve == MSM_CURVE_BLS12_381_G1 ? 16 : 32;  // one 128- or 256-bit access

@@ -17,6 +17,7 @@
 
 #include "ntt_launch.h"
 #include "ntt_plan.h"
+#include "nvtx_range.h"
 
 using namespace gb300ntt;
 
@@ -141,6 +142,7 @@ void static_batch_forget_addresses() {
 }  // namespace gb300ntt
 
 extern "C" ntt_status ntt_batch_submit_static(const ntt_job *jobs, size_t n, uint32_t *d_status, ntt_stream stream) {
+  NvtxRange range("ntt_batch_submit_static");
   if (!jobs && n) return NTT_ERR_INVALID_ARG;
   if (n > kStaticMaxJobs) return NTT_ERR_UNSUPPORTED;
   for (size_t i = 0; i < n; ++i) {

@@ -6,8 +6,9 @@
 // process each:
 //   NTT_PART_PASS = 10 or 11  the pass kernels of one tile shape;
 //   NTT_PART_BATCH            the persistent batched kernel;
-//   NTT_PART_MISC             table generators, element-wise kernels, the
-//                             matrix-form pass and the launcher table.
+//   NTT_PART_MATRIX           the matrix-form (tensor-core) pass;
+//   NTT_PART_MISC             table generators, element-wise kernels and
+//                             the launcher table.
 #include "../../include/ntt_gb300.h"
 #include "ntt_launch.h"
 
@@ -21,6 +22,8 @@ cudaError_t pass10(int logs, int mode, bool fused, const PassArgs &a, uint64_t t
 cudaError_t pass11(int logs, int mode, bool fused, const PassArgs &a, uint64_t tiles, cudaStream_t st);
 cudaError_t prepare_batch();
 cudaError_t batch(const BatchLaunch &b, cudaStream_t st);
+cudaError_t prepare_matrix();
+cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st);
 
 namespace {
 
@@ -256,6 +259,52 @@ cudaError_t prepare_batch() {
   return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
 }
 
+#elif defined(NTT_PART_MATRIX)
+
+namespace {
+
+template <int LOGS, int MODE>
+cudaError_t set_matrix_attr() {
+  return cudaFuncSetAttribute(ntt_matrix_pass_kernel<F, LOGS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              matrix_smem_bytes<LOGS>());
+}
+
+template <int LOGS>
+cudaError_t set_matrix_attrs() {
+  cudaError_t e = set_matrix_attr<LOGS, kModeInner>();
+  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirst>();
+  return e;
+}
+
+template <int LOGS>
+cudaError_t matrix_logs(int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
+  const int smem = matrix_smem_bytes<LOGS>();
+  switch (mode) {
+    case kModeInner: ntt_matrix_pass_kernel<F, LOGS, kModeInner><<<grid, kMatThreads, smem, st>>>(ma); break;
+    case kModeFirst: ntt_matrix_pass_kernel<F, LOGS, kModeFirst><<<grid, kMatThreads, smem, st>>>(ma); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
+  switch (logs) {
+    case 1: return matrix_logs<1>(mode, ma, grid, st);
+    case 2: return matrix_logs<2>(mode, ma, grid, st);
+    case 3: return matrix_logs<3>(mode, ma, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t prepare_matrix() {
+  cudaError_t e = set_matrix_attrs<1>();
+  if (e == cudaSuccess) e = set_matrix_attrs<2>();
+  if (e == cudaSuccess) e = set_matrix_attrs<3>();
+  return e;
+}
+
 #elif defined(NTT_PART_MISC)
 
 namespace {
@@ -361,46 +410,9 @@ __global__ void mul_rep_coop_kernel(uint32_t *out, const uint32_t *a, const uint
   if (live) out[elem * 8 + j] = x;
 }
 
-template <int LOGS, int MODE>
-cudaError_t set_matrix_attr() {
-  return cudaFuncSetAttribute(ntt_matrix_pass_kernel<F, LOGS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              matrix_smem_bytes<LOGS>());
-}
-
-template <int LOGS>
-cudaError_t set_matrix_attrs() {
-  cudaError_t e = set_matrix_attr<LOGS, kModeInner>();
-  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirst>();
-  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirstPre>();
-  return e;
-}
-
-template <int LOGS>
-cudaError_t matrix_logs(int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
-  const int smem = matrix_smem_bytes<LOGS>();
-  switch (mode) {
-    case kModeInner: ntt_matrix_pass_kernel<F, LOGS, kModeInner><<<grid, kMatThreads, smem, st>>>(ma); break;
-    case kModeFirst: ntt_matrix_pass_kernel<F, LOGS, kModeFirst><<<grid, kMatThreads, smem, st>>>(ma); break;
-    case kModeFirstPre: ntt_matrix_pass_kernel<F, LOGS, kModeFirstPre><<<grid, kMatThreads, smem, st>>>(ma); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
-  switch (logs) {
-    case 1: return matrix_logs<1>(mode, ma, grid, st);
-    case 2: return matrix_logs<2>(mode, ma, grid, st);
-    case 3: return matrix_logs<3>(mode, ma, grid, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 cudaError_t prepare() {
   cudaError_t e = prepare_pass11();
-  if (e == cudaSuccess) e = set_matrix_attrs<1>();
-  if (e == cudaSuccess) e = set_matrix_attrs<2>();
-  if (e == cudaSuccess) e = set_matrix_attrs<3>();
+  if (e == cudaSuccess) e = prepare_matrix();
   if (e == cudaSuccess) e = prepare_pass10();
   if (e == cudaSuccess) e = prepare_batch();
   return e;

@@ -2,10 +2,12 @@
 //
 // The matrix path runs every pass as a tensor-core product with a byte
 // matrix E (ntt_matrix.cuh).  Its passes are at most 2^3 points (K = N =
-// 32 S <= 256 keeps every fp32 partial sum exact), so a plan on this path
-// owns a nested plan with that split: the nested plan's inter-pass tables,
-// coset and inverse factors are used exactly as on the butterfly path; its
-// DFT twiddle tables are replaced by E.
+// 32 S <= 256 keeps every fp32 partial sum within 2^22), so a plan on this
+// path owns a nested plan with that split whose inter-pass, coset and
+// inverse tables are used as on the butterfly path -- except that each
+// pass's epilogue applies the NEXT pass's input factors, and the pass-0
+// factors (coset powers; N^-1 of a single-pass inverse) are folded into the
+// pass-0 matrix E.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -23,42 +25,118 @@ constexpr uint32_t kMatrixMaxPassLog = 3;
 
 namespace {
 
-int signed_digit(const U256 &v, int b, int *carry) {
-  int d = (int)((v.w[b / 8] >> (8 * (b % 8))) & 0xFF) + *carry;
-  *carry = d >= 128 ? 1 : 0;
-  return d - (*carry << 8);
+// Balanced base-256 digits of a canonical value (< 2^255): digit h in
+// [-128, 127], sum_h digit_h 2^(8h) = v.  The top digit stays below 128
+// because v < 2^255.
+void balanced_digits(const U256 &v, int out[32]) {
+  int carry = 0;
+  for (int h = 0; h < 32; ++h) {
+    int d = (int)((v.w[h / 8] >> (8 * (h % 8))) & 0xFF) + carry;
+    carry = d >= 128 ? 1 : 0;
+    out[h] = d - (carry << 8);
+  }
 }
 
-uint16_t bf16_bits(int v) {
-  float f = (float)v;
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  return (uint16_t)(u >> 16);  // exact for |v| <= 256
+// IEEE fp16 bit pattern of an integer in [-128, 128] (exact).
+uint16_t f16_bits(int v) {
+  if (v == 0) return 0;
+  const uint16_t sign = v < 0 ? 0x8000 : 0;
+  unsigned a = (unsigned)(v < 0 ? -v : v);
+  int e = 0;
+  while ((a >> (e + 1)) != 0) ++e;                      // a in [2^e, 2^(e+1))
+  const unsigned mant = (a << (10 - e)) & 0x3FF;        // 10 fraction bits
+  return (uint16_t)(sign | ((unsigned)(e + 15) << 10) | mant);
 }
 
-// E[(k,h), (n,b)] = signed digit h of omega_S^(dir * n k) * 2^(8b) * 2^256 mod p,
-// stored as the K-major B operand (N = K = 32 S rows/columns).
-std::vector<uint8_t> build_e(const HostField &F, uint32_t logs, bool inverse) {
-  const uint32_t S = 1u << logs, K = 32 * S;
-  std::vector<uint8_t> buf((size_t)K * K * 2, 0);
+// Effective pass matrix V[n][k] = pre_n omega^(nk) (row-major n * S + k).
+std::vector<U256> pass_matrix(const HostField &F, uint32_t logs, bool inverse, const std::vector<U256> &pre) {
+  const uint32_t S = 1u << logs;
   U256 w = F.root_of_unity(logs);
   if (inverse) w = F.inv(w);
+  std::vector<U256> V((size_t)S * S);
+  for (uint32_t n = 0; n < S; ++n)
+    for (uint32_t k = 0; k < S; ++k) {
+      const U256 t = F.pow(w, (uint64_t)((n * k) % S));
+      V[(size_t)n * S + k] = pre.empty() ? t : F.mul(pre[n], t);
+    }
+  return V;
+}
+
+U256 times_pow2(const HostField &F, U256 v, unsigned e) {
+  for (unsigned i = 0; i < e; ++i) v = F.add(v, v);
+  return v;
+}
+
+// E[(k,h),(n,b)] = digit h of V[n][k] 2^(8b) 2^32 mod p, fp16, in the
+// K-major B-operand layout (N = K = 32 S), and the merge offsets
+// O_k = 2^32 C sum_n V[n][k] - B sum_h 2^(8h) mod p, C = 128 sum_b 2^(8b),
+// B = 0x4B400000 (the fp32 pattern of 1.5 2^23 in every accumulator).
+void build_e16(const HostField &F, uint32_t logs, const std::vector<U256> &V, std::vector<uint8_t> *e,
+               uint32_t off[8][8]) {
+  const uint32_t S = 1u << logs, K = 32 * S;
+  e->assign((size_t)K * K * 2, 0);
   for (uint32_t n = 0; n < S; ++n) {
     for (uint32_t k = 0; k < S; ++k) {
-      U256 v = F.to_mont(F.pow(w, (uint64_t)((n * k) % S)));
+      U256 wv = times_pow2(F, V[(size_t)n * S + k], 32);
       for (uint32_t b = 0; b < 32; ++b) {
-        int carry = 0;
+        int dg[32];
+        balanced_digits(wv, dg);
         for (uint32_t h = 0; h < 32; ++h) {
-          const int dg = signed_digit(v, (int)h, &carry);
-          const uint16_t bits = bf16_bits(dg);
-          const uint32_t off = core_offset(32 * k + h, 32 * n + b, K);
-          std::memcpy(&buf[off], &bits, 2);
+          const uint16_t bits = f16_bits(dg[h]);
+          std::memcpy(&(*e)[core_offset(32 * k + h, 32 * n + b, K)], &bits, 2);
         }
-        for (int i = 0; i < 8; ++i) v = F.add(v, v);  // * 2^8
+        wv = times_pow2(F, wv, 8);
       }
     }
   }
-  return buf;
+  U256 sigma = u256(0), pw = u256(1);   // sum_{i<32} 2^(8i) mod p
+  for (int i = 0; i < 32; ++i) {
+    sigma = F.add(sigma, pw);
+    pw = times_pow2(F, pw, 8);
+  }
+  const U256 c = F.mul(F.reduce_small(128), sigma);
+  const U256 bsig = F.mul(F.reduce_small(0x4B400000u), sigma);
+  std::memset(off, 0, sizeof(uint32_t) * 64);
+  for (uint32_t k = 0; k < S; ++k) {
+    U256 colsum = u256(0);
+    for (uint32_t n = 0; n < S; ++n) colsum = F.add(colsum, V[(size_t)n * S + k]);
+    const U256 corr = times_pow2(F, F.mul(c, colsum), 32);
+    const U256 o = F.sub(corr, bsig);
+    for (int i = 0; i < 4; ++i) {
+      off[k][2 * i] = (uint32_t)o.w[i];
+      off[k][2 * i + 1] = (uint32_t)(o.w[i] >> 32);
+    }
+  }
+}
+
+ntt_status upload(ntt_plan p, const std::vector<uint8_t> &buf, uint4 **out) {
+  if (*out) {
+    cudaFree(*out);
+    *out = nullptr;
+  }
+  ntt_status s = cuda_status(cudaMalloc(out, buf.size()));
+  if (s == NTT_OK) s = cuda_status(cudaMemcpy(*out, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  return s;
+}
+
+// Pass-0 factors pre_n of table kind tk for the nested plan q (empty: all 1).
+std::vector<U256> pass0_factors(const HostField &F, ntt_plan q, int tk) {
+  const uint32_t logs0 = q->pass_log[0], S0 = 1u << logs0;
+  std::vector<U256> pre;
+  if (tk == kInverse && q->num_passes == 1) {
+    const U256 ninv = F.inv(F.reduce_small(1ull << q->log_n));
+    pre.assign(S0, ninv);
+  } else if (tk == kCoset) {
+    // s^(n N / S_0)
+    const U256 step = F.pow(q->coset_shift, 1ull << (q->log_n - logs0));
+    pre.resize(S0);
+    U256 acc = u256(1);
+    for (uint32_t n = 0; n < S0; ++n) {
+      pre[n] = acc;
+      acc = F.mul(acc, step);
+    }
+  }
+  return pre;
 }
 
 }  // namespace
@@ -69,12 +147,26 @@ void release_matrix_resources(ntt_plan p) {
   MatrixResources *m = p->matrix;
   if (!m) return;
   if (m->nested) ntt_plan_destroy(m->nested);
-  for (auto &row : m->e)
+  for (auto &row : m->e_inner)
     for (uint4 *q : row)
       if (q) cudaFree(q);
+  for (uint4 *q : m->e_first)
+    if (q) cudaFree(q);
   if (m->err) cudaFree(m->err);
   delete m;
   p->matrix = nullptr;
+}
+
+// (Re)build the pass-0 matrix of the coset kind (after a coset-shift change).
+ntt_status matrix_build_coset(ntt_plan p) {
+  MatrixResources *m = p->matrix;
+  if (!m || !m->nested || !p->has_coset) return NTT_OK;
+  const HostField F = host_field(p->field);
+  ntt_plan q = m->nested;
+  std::vector<uint8_t> buf;
+  const std::vector<U256> V = pass_matrix(F, q->pass_log[0], false, pass0_factors(F, q, kCoset));
+  build_e16(F, q->pass_log[0], V, &buf, m->off_first[kCoset]);
+  return upload(p, buf, &m->e_first[kCoset]);
 }
 
 static ntt_status ensure_matrix(ntt_plan p) {
@@ -105,32 +197,32 @@ static ntt_status ensure_matrix(ntt_plan p) {
   }
   if (s != NTT_OK) return s;
   const HostField F = host_field(p->field);
-  for (uint32_t j = 0; j < q->num_passes; ++j) {
+  std::vector<uint8_t> buf;
+  // inner passes: plain DFT matrices per direction and size
+  for (uint32_t j = 1; j < q->num_passes; ++j) {
     const uint32_t logs = q->pass_log[j];
     for (int dir = 0; dir < 2; ++dir) {
-      if (m->e[dir][logs]) continue;
-      const std::vector<uint8_t> buf = build_e(F, logs, dir == 1);
-      s = cuda_status(cudaMalloc(&m->e[dir][logs], buf.size()));
-      if (s == NTT_OK) s = cuda_status(cudaMemcpy(m->e[dir][logs], buf.data(), buf.size(), cudaMemcpyHostToDevice));
+      if (m->e_inner[dir][logs]) continue;
+      build_e16(F, logs, pass_matrix(F, logs, dir == 1, {}), &buf, m->off_inner[dir][logs]);
+      s = upload(p, buf, &m->e_inner[dir][logs]);
       if (s != NTT_OK) return s;
       p->device_bytes += buf.size();
     }
   }
-  U256 off = F.p;  // 2^18 * p (< 2^274), nine limbs
-  uint32_t limbs[9] = {};
+  // pass 0: one matrix per table kind, its factors folded in
+  for (int tk = kForward; tk <= kCoset; ++tk) {
+    if (tk == kCoset && !p->has_coset) continue;
+    const std::vector<U256> V = pass_matrix(F, q->pass_log[0], tk == kInverse, pass0_factors(F, q, tk));
+    build_e16(F, q->pass_log[0], V, &buf, m->off_first[tk]);
+    s = upload(p, buf, &m->e_first[tk]);
+    if (s != NTT_OK) return s;
+    p->device_bytes += buf.size();
+  }
+  const U256 one = F.to_mont(u256(1));
   for (int i = 0; i < 4; ++i) {
-    limbs[2 * i] = (uint32_t)off.w[i];
-    limbs[2 * i + 1] = (uint32_t)(off.w[i] >> 32);
+    m->one[2 * i] = (uint32_t)one.w[i];
+    m->one[2 * i + 1] = (uint32_t)(one.w[i] >> 32);
   }
-  for (int sh = 0; sh < 18; ++sh) {
-    uint32_t c = 0;
-    for (int i = 0; i < 9; ++i) {
-      const uint32_t nc = limbs[i] >> 31;
-      limbs[i] = (limbs[i] << 1) | c;
-      c = nc;
-    }
-  }
-  std::memcpy(m->offset, limbs, sizeof limbs);
   s = cuda_status(cudaMalloc(&m->err, sizeof(uint32_t)));
   if (s == NTT_OK) s = cuda_status(cudaMemset(m->err, 0, sizeof(uint32_t)));
   p->device_bytes += q->device_bytes;
@@ -158,14 +250,30 @@ ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *
   if (!m || !m->nested) return NTT_ERR_UNSUPPORTED;
   ntt_plan q = m->nested;
   const FieldLaunchers &L = launchers(p->field);
-  const int dir = table_kind(kind) == kInverse ? 1 : 0;
+  const int tk = table_kind(kind);
+  const int dir = tk == kInverse ? 1 : 0;
+  uint32_t log_m = 0;
   for (uint32_t j = 0; j < q->num_passes; ++j) {
     MatrixPassArgs ma{};
     int mode = 0;
     build_pass_args(q, kind, in, out, j, &ma.a, &mode);
     const uint32_t logs = q->pass_log[j];
-    ma.e = m->e[dir][logs];
-    std::memcpy(ma.offset, m->offset, sizeof ma.offset);
+    log_m += logs;
+    if (j == 0) {
+      ma.e = m->e_first[tk];
+      std::memcpy(ma.off, m->off_first[tk], sizeof ma.off);
+      mode = kModeFirst;   // the pass-0 factors are in E
+    } else {
+      ma.e = m->e_inner[dir][logs];
+      std::memcpy(ma.off, m->off_inner[dir][logs], sizeof ma.off);
+    }
+    if (!ma.e) return NTT_ERR_UNSUPPORTED;
+    if (j + 1 < q->num_passes) {
+      ma.next = q->tw[tk][j + 1];
+      ma.next_log = log_m + q->pass_log[j + 1];
+    }
+    ma.post = ma.a.post;   // last pass of a coset inverse: s^-n
+    std::memcpy(ma.one, m->one, sizeof ma.one);
     ma.err = m->err;
     ma.wait_ns = 1000000000ull;
     const uint64_t tiles = (ma.a.num_sub + kMatRows - 1) / kMatRows;

@@ -2,29 +2,52 @@
 //
 // The paper's reformulation (Sec. 3.2.3-3.2.4, Alg. 1; Sec. 3.3.2, Fig. 5b-c):
 // high-precision modular arithmetic becomes a low-precision matrix product
-// over byte limbs (ByteDecompose -> uint8 "Einsum" against a precomputed
-// byte matrix E -> ByteMerge), and the NTT's sub-transforms become matrix
-// products with twiddle matrices.  Here one pass of the multi-pass NTT
-// computes, for 128 sub-transforms of size S at once,
+// over byte limbs (ByteDecompose -> byte "Einsum" against a precomputed byte
+// matrix -> ByteMerge), and the NTT's sub-transforms become products with
+// twiddle matrices.  One pass of the multi-pass NTT computes, for 128
+// sub-transforms of S points at once (S = 2, 4 or 8),
 //
-//   y_k = sum_n x_n omega_S^(nk)
-//       = sum_{n,b} a_{n,b} W[(n,b), k],  x_n = sum_b a_{n,b} 2^(8b)
-//   W[(n,b), k] = omega_S^(nk) * 2^(8b) * 2^256 mod p       (precomputed)
-//   W[(n,b), k] = sum_h E[(k,h), (n,b)] 2^(8h)              (signed digits)
-//   acc[k,h]   = sum_{n,b} a_{n,b} E[(k,h), (n,b)]           <- tensor cores
-//   y_k        = REDC( sum_h acc[k,h] 2^(8h) + 2^18 p )      <- ByteMerge + Montgomery
+//   y_k = sum_n V[n,k] x_n,   V[n,k] = pre_n omega_S^(nk)   (pre_n: pass-0
+//         coset / scale factors folded in; 1 for the other passes)
+//   x_n = sum_b (a_{n,b} + 128) 2^(8b),   a_{n,b} = byte b of x_n - 128
+//   W[(n,b),k] = V[n,k] 2^(8b) 2^32 mod p  = sum_h E[(k,h),(n,b)] 2^(8h)
+//                 (E: balanced signed byte digits of W, in [-128, 127])
+//   acc[k,h] = sum_{n,b} a_{n,b} E[(k,h),(n,b)]     <- tcgen05.mma kind::f16
+//   Z_k = sum_h (acc[k,h] + 2^23 1.5 (as fp32 bits)) 2^(8h) + O_k
+//       = 2^32 y_k (mod p),   O_k = (2^32 C sum_n V[n,k] - B sum_h 2^(8h)) mod p
+//   out = Z_k * T * 2^-288 mod p                      <- 9-row Montgomery
 //
-// Digits are balanced (signed, in [-128, 127]) so |a * E| <= 2^14 and, with
-// K = 32 S <= 256 terms, every partial sum stays within 2^22: bf16 holds the
-// digits exactly and the fp32 accumulators hold every partial sum exactly
-// (checked on GB300 with adversarial all -128 operands).  The 2^256 in W
-// cancels the REDC factor, so the output is the standard-form y_k, canonical.
+// where C = 128 sum_b 2^(8b) undoes the digit offset and B = 0x4B400000 is
+// the fp32 bit pattern of 1.5 * 2^23.  T is the Montgomery form c 2^256 of the
+// factor the element needs next: the NEXT pass's inter-pass twiddle (looked
+// up by the output position), the coset inverse's s^-n in the last pass, or
+// 1.  So the inter-pass twiddle product of the paper's 3-/5-step NTT is fused
+// with the reduction of the ByteMerge result: one Montgomery product per
+// element per pass, nothing else on the integer multiply pipe.
 //
-// Shapes per CTA tile: M = 128 (sub-transforms), N = K = 32 S (S <= 8),
-// one tcgen05.mma.cta_group::1.kind::f16 (bf16 x bf16 -> f32) per 16 of K,
-// accumulator in TMEM (N columns), operands in shared memory in the K-major
-// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix, LBO =
-// 128 bytes along K, SBO = K/8 * 128 bytes along M/N).
+// Exactness: |a E| <= 2^14 and K = 32 S <= 256 terms keep every partial sum
+// within 2^22, exact in fp16 x fp16 -> fp32 accumulation; fp16 holds the byte
+// digits exactly (integers up to 2^11).  With |acc| <= 2^22, acc + 1.5 2^23
+// lies in [2^23, 2^24), so its fp32 bit pattern is 0x4B400000 + acc exactly
+// (one FADD, no float-to-integer conversion).  Z < 2^31 2^248 (256/255) + p <
+// 2^280, so the 9-row Montgomery product (R = 2^288) of Z and T < p ends below
+// 2p and one conditional subtraction makes it canonical.
+//
+// Kernel structure (persistent, one CTA per SM, warp-specialised):
+//   warp 0       TMA loader: cp.async.bulk of each chunk's inputs (128 rows
+//                of one input n, contiguous runs) into a staging ring; also
+//                loads E (resident for the whole kernel);
+//   warp 1       MMA issuer: two tcgen05.mma (K = 16 each) per chunk into a
+//                double-buffered TMEM accumulator (N = 32 S columns each);
+//   warps 2-5    digit converters: staging element -> 32 fp16 digits by byte
+//                permutes (0x64 | byte = 1024 + byte as fp16) and one packed
+//                fp16 subtraction, written as the A operand chunk;
+//   warps 6-21   epilogue: tcgen05.ld of one output's 32 accumulators,
+//                ByteMerge by funnel shifts and carry chains, the Montgomery
+//                product with T, store.
+// Every wait is an mbarrier wait bounded by %globaltimer; on timeout the CTA
+// records NTT_ERR_TIMEOUT, every role stops, copies in flight are waited for
+// (bounded) and TMEM is freed before the kernel returns.
 #pragma once
 
 #include <cstdint>
@@ -35,15 +58,26 @@
 
 namespace gb300ntt {
 
-constexpr int kMatThreads = 512;
-constexpr int kMatRows = 128;  // sub-transforms per tile (MMA M)
+constexpr int kMatRows = 128;                 // sub-transforms per tile (MMA M)
+constexpr int kMatConvWarps = 4;              // one converter thread per tile row
+constexpr int kMatEpiWarps = 16;              // four per TMEM lane quarter
+constexpr int kMatFirstEpiWarp = 2 + kMatConvWarps;
+constexpr int kMatThreads = 32 * (kMatFirstEpiWarp + kMatEpiWarps);   // 704
+constexpr int kMatRing = 8;                   // chunks in flight (A operand and staging)
+constexpr uint32_t kMatChunkBytes = kMatRows * 32 * 2;   // A chunk: 128 rows x 32 fp16 digits
+constexpr uint32_t kMatStageBytes = kMatRows * 32;       // staging: 128 elements
+constexpr uint32_t kMatFp32Magic = 0x4B400000u;          // bits of 1.5 * 2^23
 
 struct MatrixPassArgs {
-  PassArgs a;                // src, dst, mul, num_sub, log_mp, digits (dft_tw unused)
-  const uint4 *e;            // E in the B-operand layout, N x K bf16
-  uint32_t offset[9];        // 2^18 * p, 9 limbs
-  uint32_t *err;             // device error word
-  uint64_t wait_ns;          // bound of the MMA-completion wait
+  PassArgs a;             // src, dst, num_sub, log_mp, digits (mul, dft_tw, post unused)
+  const uint4 *e;         // E, fp16, B-operand layout (N x K = 32 S x 32 S)
+  const uint4 *next;      // epilogue factor table indexed by pos mod 2^next_log, or null
+  const uint4 *post;      // epilogue factor table indexed by pos (coset inverse), or null
+  uint32_t next_log;
+  uint32_t off[8][8];     // O_k (canonical), k < S
+  uint32_t one[8];        // 2^256 mod p: the factor when no table applies
+  uint32_t *err;          // device error word
+  uint64_t wait_ns;       // bound of every wait
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -57,73 +91,11 @@ __device__ __forceinline__ uint64_t mat_desc(uint32_t addr, uint32_t lbo, uint32
   return d;
 }
 
-// Byte offset of element (row, col) of a K-major bf16 operand with K columns.
+// Byte offset of element (row, col) of a K-major 16-bit operand with K
+// columns (core matrices of 8 rows x 16 bytes, K-direction neighbours 128
+// bytes apart, 8-row groups K/8 * 128 bytes apart).
 __host__ __device__ __forceinline__ uint32_t core_offset(uint32_t row, uint32_t col, uint32_t K) {
   return ((row >> 3) * (K >> 3) + (col >> 3)) * 128 + (row & 7) * 16 + (col & 7) * 2;
-}
-
-// bf16 bit pattern of a small integer v in [-128, 127] (exact).
-__device__ __forceinline__ uint32_t bf16_of_small_int(int v) {
-  if (v == 0) return 0;
-  const uint32_t s = v < 0 ? 0x8000u : 0u;
-  const uint32_t a = (uint32_t)(v < 0 ? -v : v);  // 1..128
-  const uint32_t e = 31 - __clz(a);                // 0..7
-  return s | ((127 + e) << 7) | ((a << (7 - e)) & 0x7Fu);
-}
-
-// Signed (balanced) base-256 digits of a canonical element (< 2^255), packed
-// as bf16 pairs: out[w] = digit 2w | digit 2w+1 << 16.
-__device__ __forceinline__ void signed_digits_bf16(uint32_t out[16], const uint32_t x[8]) {
-  int carry = 0;
-#pragma unroll
-  for (int w = 0; w < 16; ++w) {
-    uint32_t pair = 0;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int b = 2 * w + j;
-      int d = (int)((x[b >> 2] >> (8 * (b & 3))) & 0xFFu) + carry;
-      carry = d >= 128 ? 1 : 0;
-      d -= carry << 8;
-      pair |= bf16_of_small_int(d) << (16 * j);
-    }
-    out[w] = pair;
-  }
-}
-
-// Exact integer of an fp32 accumulator with |v| <= 2^22.
-__device__ __forceinline__ int acc_to_int(uint32_t bits) {
-  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
-}
-
-// y = REDC(sum_h acc[h] 2^(8h) + offset) for the 32 accumulators of one output.
-template <class F>
-__device__ __forceinline__ void merge_reduce(uint32_t y[8], const uint32_t acc_bits[32], const uint32_t offset[9]) {
-  int64_t col[8];
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    col[l] = (int64_t)acc_to_int(acc_bits[4 * l]) + ((int64_t)acc_to_int(acc_bits[4 * l + 1]) << 8) +
-             ((int64_t)acc_to_int(acc_bits[4 * l + 2]) << 16) + ((int64_t)acc_to_int(acc_bits[4 * l + 3]) << 24);
-  }
-  uint32_t t[9];
-  int64_t carry = 0;
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    const int64_t v = col[l] + (int64_t)offset[l] + carry;
-    t[l] = (uint32_t)v;
-    carry = v >> 32;
-  }
-  t[8] = (uint32_t)((int64_t)offset[8] + carry);
-  // Montgomery reduction of the 9-limb value (< 2^274 < p * 2^256)
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const uint32_t m = mont_m<F>(t[0]);
-    row_even_p<F>(t, m);
-    row_odd_p<F>(t, m);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) t[j] = t[j + 1];
-    t[8] = 0;
-  }
-  reduce_once<F>(y, t);
 }
 
 __device__ __forceinline__ uint64_t mat_global_ns() {
@@ -132,36 +104,231 @@ __device__ __forceinline__ uint64_t mat_global_ns() {
   return t;
 }
 
-// One matrix pass: persistent CTAs (one per SM) loop over tiles of 128
-// sub-transforms.  MODE as in ntt_pass.cuh (input multiplier variants).
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for completion of the phase of `bar` with the given parity, bounded
+// by wait_ns; gives up early when another role has aborted.  On timeout the
+// CTA's abort flag and the device error word are set.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const MatrixPassArgs &ma,
+                                          volatile int *abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = mat_global_ns();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (mat_global_ns() - t0 > ma.wait_ns) {
+      *abort = 1;
+      atomicCAS(ma.err, 0u, (uint32_t)NTT_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// Global -> shared bulk copy (TMA, this GPU's memory only, no multicast),
+// completing on `bar` (bytes counted by its expect_tx).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// 32 fp16 digits (byte - 128) of one element, packed in 16 words: word 2i
+// holds bytes 4i, 4i+1 of limb i, word 2i+1 bytes 4i+2, 4i+3.  The byte
+// permute builds the fp16 pattern 0x64bb = 1024 + byte; subtracting 1152
+// (0x6480) in packed fp16 leaves byte - 128 exactly.
+__device__ __forceinline__ void digits_f16(uint32_t w[16], const uint32_t x[8]) {
+  const uint32_t k1152 = 0x64806480u, k64 = 0x64646464u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    uint32_t lo, hi;
+    asm("prmt.b32 %0, %1, %2, 0x4140;" : "=r"(lo) : "r"(x[i]), "r"(k64));
+    asm("prmt.b32 %0, %1, %2, 0x4342;" : "=r"(hi) : "r"(x[i]), "r"(k64));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * i]) : "r"(lo), "r"(k1152));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * i + 1]) : "r"(hi), "r"(k1152));
+  }
+}
+
+// Z = sum_h u_h 2^(8h) + off, u_h = fp32 bits of acc_h + 1.5 2^23 (< 2^31).
+// Four non-overlapping 9-limb terms: A = u_{4l} at limb l, and for the
+// byte shifts 8, 16, 24 the funnel-shifted limbs (u_{4l+j} << 8j) |
+// (u_{4l+j-4} >> (32 - 8j)); summed with carry chains.
+__device__ __forceinline__ void byte_merge(uint32_t z[9], const uint32_t u[32], const uint32_t off[8]) {
+  uint32_t b[9], c[9], d[9];
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    const uint32_t b_lo = l < 8 ? u[4 * l + 1] : 0u, b_hi = l > 0 ? u[4 * l - 3] : 0u;
+    const uint32_t c_lo = l < 8 ? u[4 * l + 2] : 0u, c_hi = l > 0 ? u[4 * l - 2] : 0u;
+    const uint32_t d_lo = l < 8 ? u[4 * l + 3] : 0u, d_hi = l > 0 ? u[4 * l - 1] : 0u;
+    b[l] = __funnelshift_l(b_hi, b_lo, 8);
+    c[l] = __funnelshift_l(c_hi, c_lo, 16);
+    d[l] = __funnelshift_l(d_hi, d_lo, 24);
+  }
+  asm("add.cc.u32  %0, %9,  %18;\n\t"
+      "addc.cc.u32 %1, %10, %19;\n\t"
+      "addc.cc.u32 %2, %11, %20;\n\t"
+      "addc.cc.u32 %3, %12, %21;\n\t"
+      "addc.cc.u32 %4, %13, %22;\n\t"
+      "addc.cc.u32 %5, %14, %23;\n\t"
+      "addc.cc.u32 %6, %15, %24;\n\t"
+      "addc.cc.u32 %7, %16, %25;\n\t"
+      "addc.u32    %8, %17, %26;"
+      : "=r"(z[0]), "=r"(z[1]), "=r"(z[2]), "=r"(z[3]), "=r"(z[4]), "=r"(z[5]), "=r"(z[6]), "=r"(z[7]), "=r"(z[8])
+      : "r"(u[0]), "r"(u[4]), "r"(u[8]), "r"(u[12]), "r"(u[16]), "r"(u[20]), "r"(u[24]), "r"(u[28]), "r"(0u),
+        "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]));
+  asm("add.cc.u32  %0, %0, %9;\n\t"
+      "addc.cc.u32 %1, %1, %10;\n\t"
+      "addc.cc.u32 %2, %2, %11;\n\t"
+      "addc.cc.u32 %3, %3, %12;\n\t"
+      "addc.cc.u32 %4, %4, %13;\n\t"
+      "addc.cc.u32 %5, %5, %14;\n\t"
+      "addc.cc.u32 %6, %6, %15;\n\t"
+      "addc.cc.u32 %7, %7, %16;\n\t"
+      "addc.u32    %8, %8, %17;"
+      : "+r"(z[0]), "+r"(z[1]), "+r"(z[2]), "+r"(z[3]), "+r"(z[4]), "+r"(z[5]), "+r"(z[6]), "+r"(z[7]), "+r"(z[8])
+      : "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(c[5]), "r"(c[6]), "r"(c[7]), "r"(c[8]));
+  asm("add.cc.u32  %0, %0, %9;\n\t"
+      "addc.cc.u32 %1, %1, %10;\n\t"
+      "addc.cc.u32 %2, %2, %11;\n\t"
+      "addc.cc.u32 %3, %3, %12;\n\t"
+      "addc.cc.u32 %4, %4, %13;\n\t"
+      "addc.cc.u32 %5, %5, %14;\n\t"
+      "addc.cc.u32 %6, %6, %15;\n\t"
+      "addc.cc.u32 %7, %7, %16;\n\t"
+      "addc.u32    %8, %8, %17;"
+      : "+r"(z[0]), "+r"(z[1]), "+r"(z[2]), "+r"(z[3]), "+r"(z[4]), "+r"(z[5]), "+r"(z[6]), "+r"(z[7]), "+r"(z[8])
+      : "r"(d[0]), "r"(d[1]), "r"(d[2]), "r"(d[3]), "r"(d[4]), "r"(d[5]), "r"(d[6]), "r"(d[7]), "r"(d[8]));
+  asm("add.cc.u32  %0, %0, %9;\n\t"
+      "addc.cc.u32 %1, %1, %10;\n\t"
+      "addc.cc.u32 %2, %2, %11;\n\t"
+      "addc.cc.u32 %3, %3, %12;\n\t"
+      "addc.cc.u32 %4, %4, %13;\n\t"
+      "addc.cc.u32 %5, %5, %14;\n\t"
+      "addc.cc.u32 %6, %6, %15;\n\t"
+      "addc.cc.u32 %7, %7, %16;\n\t"
+      "addc.u32    %8, %8, 0;"
+      : "+r"(z[0]), "+r"(z[1]), "+r"(z[2]), "+r"(z[3]), "+r"(z[4]), "+r"(z[5]), "+r"(z[6]), "+r"(z[7]), "+r"(z[8])
+      : "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3]), "r"(off[4]), "r"(off[5]), "r"(off[6]), "r"(off[7]));
+}
+
+// r = z * t * 2^-288 mod p for z < 2^280 (nine limbs) and canonical t: the
+// CIOS rows of mont_mul (fp256.cuh) over the nine limbs of z.  The running
+// value stays below 2^288 (as in mont_mul: t < p, one limb of z per row) and
+// the result is below 2p, so one conditional subtraction makes it canonical.
+template <class F>
+__device__ __forceinline__ void mont_mul_z9(uint32_t r[8], const uint32_t z[9], const uint32_t t[8]) {
+  uint32_t acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    row_even(acc, t, z[i]);
+    row_odd(acc, t, z[i]);
+    const uint32_t m = mont_m<F>(acc[0]);
+    row_even_p<F>(acc, m);
+    row_odd_p<F>(acc, m);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = acc[j + 1];
+    acc[8] = 0;
+  }
+  reduce_once<F>(r, acc);
+}
+
+// Position of input n (or, for inner passes, output n) of sub-transform d.
+template <int LOGS, int MODE>
+__device__ __forceinline__ uint64_t mat_in_pos(const PassArgs &a, uint64_t d, uint32_t n) {
+  if constexpr (MODE == kModeInner) {
+    const uint64_t q = d & ((1ull << a.log_mp) - 1), o = d >> a.log_mp;
+    return q + ((uint64_t)n << a.log_mp) + (o << (a.log_mp + LOGS));
+  } else {
+    return d + ((uint64_t)n << a.log_mp);
+  }
+}
+
+template <int LOGS, int MODE>
+__device__ __forceinline__ uint64_t mat_out_pos(const PassArgs &a, uint64_t d, uint32_t k) {
+  if constexpr (MODE == kModeInner) return mat_in_pos<LOGS, MODE>(a, d, k);
+  else return (reverse_digits(a, d) << LOGS) | k;
+}
+
+template <int LOGS>
+__host__ __device__ constexpr uint32_t matrix_tmem_cols() {
+  // two accumulators of 32 S columns, at least 32 columns in all, power of two
+  return (64u << LOGS) < 32u ? 32u : (64u << LOGS);
+}
+
+template <int LOGS>
+__host__ __device__ constexpr int matrix_smem_bytes() {
+  return (32 << LOGS) * (32 << LOGS) * 2 + kMatRing * (int)(kMatChunkBytes + kMatStageBytes);
+}
+
+// One matrix pass (MODE: kModeInner or kModeFirst; pass-0 multipliers are
+// folded into E).
 template <class F, int LOGS, int MODE>
 __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const MatrixPassArgs ma) {
   constexpr uint32_t S = 1u << LOGS;
-  constexpr uint32_t K = 32 * S;                 // (n, b)
-  constexpr uint32_t NCOL = 32 * S;              // (k, h)
-  constexpr uint32_t TMEM_COLS = NCOL < 32 ? 32 : NCOL;
-  constexpr uint32_t E_BYTES = NCOL * K * 2;
-  constexpr uint32_t A_BYTES = kMatRows * K * 2;
-  static_assert(NCOL <= 256, "one MMA per K step");
-  static_assert(E_BYTES + A_BYTES <= 227u * 1024u, "E and the A tile fit in shared memory");
+  constexpr uint32_t K = 32 * S;                  // (n, b)
+  constexpr uint32_t NC = 32 * S;                 // (k, h)
+  constexpr uint32_t TMEM_COLS = matrix_tmem_cols<LOGS>();
+  constexpr uint32_t E_BYTES = NC * K * 2;
+  static_assert(NC <= 256 && NC % 16 == 0, "one MMA covers all outputs");
+  static_assert(matrix_smem_bytes<LOGS>() <= 227 * 1024 - 512, "shared memory");
   extern __shared__ __align__(1024) uint8_t mat_smem[];
   uint8_t *sE = mat_smem;
-  uint8_t *sA = mat_smem + E_BYTES;                   // also the output staging area
+  uint8_t *sA = mat_smem + E_BYTES;
+  uint8_t *sStage = sA + kMatRing * kMatChunkBytes;
+  __shared__ __align__(8) uint64_t bar_e;
+  __shared__ __align__(8) uint64_t stage_full[kMatRing], stage_empty[kMatRing];
+  __shared__ __align__(8) uint64_t chunk_full[kMatRing], chunk_empty[kMatRing];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t bar_done;
   __shared__ uint32_t s_taddr;
-  __shared__ __align__(8) uint64_t s_mbar;
   __shared__ int s_abort;
+  volatile int *abort = &s_abort;
   const PassArgs &a = ma.a;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t num_tiles = (a.num_sub + kMatRows - 1) / kMatRows;
+  // tiles of this CTA
+  const uint64_t my_tiles = blockIdx.x < num_tiles ? (num_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-  // resident E
-  for (uint32_t i = tid; i < E_BYTES / 16; i += kMatThreads)
-    reinterpret_cast<uint4 *>(sE)[i] = __ldg(ma.e + i);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init(&bar_e, 1);
+    for (int i = 0; i < kMatRing; ++i) {
+      mbar_init(&stage_full[i], 1);
+      mbar_init(&stage_empty[i], 32 * kMatConvWarps);
+      mbar_init(&chunk_full[i], 32 * kMatConvWarps);
+      mbar_init(&chunk_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 32 * kMatEpiWarps);
+    }
+    mbar_init(&bar_done, 1);
     s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_taddr)),
                  "n"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -170,89 +337,140 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = s_taddr;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((NCOL >> 3) << 17) | ((uint32_t)(kMatRows >> 4) << 24);
-  const uint64_t num_tiles = (a.num_sub + kMatRows - 1) / kMatRows;
-  const uint64_t mp_mask = (1ull << a.log_mp) - 1;
-  uint32_t phase = 0;
 
-  for (uint64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
-    const uint64_t d0 = tile * kMatRows;
-    // ---- A: load, multiply, split into signed digits (row m, K range 32n..32n+31)
-    for (uint32_t e = tid; e < kMatRows * S; e += kMatThreads) {
-      const uint32_t n = e / kMatRows, m = e % kMatRows;   // consecutive threads: consecutive m
-      const uint64_t d = d0 + m;
-      uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (d < a.num_sub) {
+  uint64_t loads_issued = 0;   // (loader thread) stage uses, for the teardown
+  if (warp == 0) {
+    // ------------------------------------------------------ TMA loader
+    if (lane == 0) {
+      mbar_expect_tx(&bar_e, E_BYTES);
+      for (uint32_t off = 0; off < E_BYTES; off += 16384u) {
+        const uint32_t bytes = E_BYTES - off < 16384u ? E_BYTES - off : 16384u;
+        bulk_g2s(sE + off, reinterpret_cast<const uint8_t *>(ma.e) + off, bytes, &bar_e);
+      }
+      uint64_t g = 0;
+      for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
+        const uint64_t d0 = (blockIdx.x + it * gridDim.x) * kMatRows;
+        const uint64_t rest = a.num_sub - d0;
+        const uint32_t valid = rest < (uint64_t)kMatRows ? (uint32_t)rest : (uint32_t)kMatRows;
+        uint32_t run = valid;
         if constexpr (MODE == kModeInner) {
-          const uint64_t q = d & mp_mask, o = d >> a.log_mp;
-          fe_load_global(v, a.src, q + ((uint64_t)n << a.log_mp) + (o << (a.log_mp + LOGS)));
-          uint32_t w[8];
-          fe_load_global(w, a.mul, ((uint64_t)n << a.log_mp) + q);
-          mont_mul<F>(v, v, w);
-        } else {
-          fe_load_global(v, a.src, d + ((uint64_t)n << a.log_mp));
-          if constexpr (MODE == kModeFirstPre) {
-            uint32_t w[8];
-            fe_load_global(w, a.mul, n);
-            mont_mul<F>(v, v, w);
-          }
+          const uint64_t mp = 1ull << a.log_mp;
+          if (mp < run) run = (uint32_t)mp;
+        }
+        for (uint32_t n = 0; n < S; ++n, ++g) {
+          const uint32_t s = (uint32_t)(g % kMatRing);
+          const uint64_t u = g / kMatRing;
+          if (u >= 1 && !mbar_wait(&stage_empty[s], (uint32_t)((u - 1) & 1), ma, abort)) break;
+          mbar_expect_tx(&stage_full[s], valid * 32u);
+          uint8_t *dst = sStage + s * kMatStageBytes;
+          for (uint32_t r0 = 0; r0 < valid; r0 += run)
+            bulk_g2s(dst + r0 * 32u, a.src + 2 * mat_in_pos<LOGS, MODE>(a, d0 + r0, n), run * 32u, &stage_full[s]);
+          loads_issued = g + 1;
         }
       }
-      uint32_t dg[16];
-      signed_digits_bf16(dg, v);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      // fp32 accumulate (bit 4), fp16 A and B (formats 0), K-major both,
+      // N >> 3 at bit 17, M >> 4 at bit 24
+      constexpr uint32_t idesc = (1u << 4) | ((NC >> 3) << 17) | ((uint32_t)(kMatRows >> 4) << 24);
+      bool ok = mbar_wait(&bar_e, 0, ma, abort);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sE);
+      uint64_t g = 0;
+      for (uint64_t it = 0; ok && it < my_tiles; ++it) {
+        const uint32_t buf = (uint32_t)(it & 1);
+        const uint64_t v = it >> 1;
+        if (v >= 1 && !mbar_wait(&acc_empty[buf], (uint32_t)((v - 1) & 1), ma, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dcol = taddr + buf * NC;
+        for (uint32_t n = 0; n < S; ++n, ++g) {
+          const uint32_t c = (uint32_t)(g % kMatRing);
+          const uint64_t u = g / kMatRing;
+          if (!mbar_wait(&chunk_full[c], (uint32_t)(u & 1), ma, abort)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {   // 4 core-matrix rows of 8 digits each
-        *reinterpret_cast<uint4 *>(sA + core_offset(m, 32 * n + 8 * c, K)) =
-            make_uint4(dg[4 * c], dg[4 * c + 1], dg[4 * c + 2], dg[4 * c + 3]);
+          for (uint32_t ks = 0; ks < 2; ++ks) {
+            const uint64_t da = mat_desc(a_base + c * kMatChunkBytes + ks * 256, 128, 4 * 128);
+            const uint64_t db = mat_desc(b_base + (2 * n + ks) * 256, 128, (K >> 3) * 128);
+            const uint32_t accum = (n | ks) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                "l"(da), "l"(db), "r"(idesc), "r"(accum));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_addr(&chunk_empty[c]))
+                       : "memory");
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(&acc_full[buf]))
+                     : "memory");
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- tensor cores: acc[m][(k,h)] = sum over K of A[m][(n,b)] * E[(k,h)][(n,b)]
-    if (tid == 0) {
-      const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sE);
-      const uint32_t sbo = (K >> 3) * 128;
-#pragma unroll 1
-      for (uint32_t ks = 0; ks < K / 16; ++ks) {
-        const uint64_t da = mat_desc(a0 + ks * 256, 128, sbo);
-        const uint64_t db = mat_desc(b0 + ks * 256, 128, sbo);
-        const uint32_t accum = ks ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
-            "l"(da), "l"(db), "r"(idesc), "r"(accum));
+  } else if (warp < kMatFirstEpiWarp) {
+    // ------------------------------------------------------ digit converters
+    const uint32_t m = tid - 64;   // tile row
+    uint64_t g = 0;
+    for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
+      bool ok = true;
+      for (uint32_t n = 0; n < S; ++n, ++g) {
+        const uint32_t c = (uint32_t)(g % kMatRing);
+        const uint64_t u = g / kMatRing;
+        if (!mbar_wait(&stage_full[c], (uint32_t)(u & 1), ma, abort)) {
+          ok = false;
+          break;
+        }
+        const uint4 *st = reinterpret_cast<const uint4 *>(sStage + c * kMatStageBytes) + 2 * m;
+        const uint4 lo = st[0], hi = st[1];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&stage_empty[c]);
+        const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        uint32_t w[16];
+        digits_f16(w, x);
+        if (u >= 1 && !mbar_wait(&chunk_empty[c], (uint32_t)((u - 1) & 1), ma, abort)) {
+          ok = false;
+          break;
+        }
+        uint8_t *dst = sA + c * kMatChunkBytes;
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4 *>(dst + core_offset(m, 8 * q, 32)) =
+              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&chunk_full[c]);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(&s_mbar)));
+      if (!ok) break;
     }
-    // ---- bounded wait for the MMAs
-    {
-      uint32_t done = 0;
-      const uint64_t t0 = mat_global_ns();
-      for (;;) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_addr(&s_mbar)), "r"(phase));
-        if (done || mat_global_ns() - t0 > ma.wait_ns) break;
-      }
-      if (!done) {
-        atomicCAS(ma.err, 0u, (uint32_t)NTT_ERR_TIMEOUT);
-        s_abort = 1;
-      }
-    }
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (s_abort) break;
-    // ---- epilogue: warps w, w+4, w+8, w+12 share TMEM lanes 32*(w%4)..; they
-    // split the S outputs of each row.
-    {
-      const uint32_t lg = warp & 3, part = warp >> 2;  // part in 0..3
-      const uint32_t m = 32 * lg + lane;
+  } else {
+    // ------------------------------------------------------ epilogue
+    const uint32_t ew = warp - kMatFirstEpiWarp;   // 0..15
+    const uint32_t quarter = warp & 3;              // TMEM lanes 32 quarter .. + 31
+    const uint32_t part = ew >> 2;                  // 0..3: outputs k = part, part + 4
+    const uint32_t m = 32 * quarter + lane;
+    const uint64_t next_mask = (1ull << ma.next_log) - 1;
+    for (uint64_t it = 0; it < my_tiles; ++it) {
+      const uint32_t buf = (uint32_t)(it & 1);
+      if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t d = (blockIdx.x + it * gridDim.x) * kMatRows + m;
+      const bool live = d < a.num_sub;
       for (uint32_t k = part; k < S; k += 4) {
+        const uint64_t pos = live ? mat_out_pos<LOGS, MODE>(a, d, k) : 0;
+        uint32_t t[8];
+        if (ma.post) {
+          if (live) fe_load_global(t, ma.post, pos);
+        } else if (ma.next) {
+          if (live) fe_load_global(t, ma.next, pos & next_mask);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[j] = ma.one[j];
+        }
         uint32_t r[32];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -262,53 +480,54 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
               "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
               "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
               "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr + ((32 * lg) << 16) + 32 * k));
+            : "r"(taddr + ((32 * quarter) << 16) + buf * NC + 32 * k));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        uint32_t y[8];
-        merge_reduce<F>(y, r, ma.offset);
-        tile_store(reinterpret_cast<uint4 *>(sA), m * S + k, y);
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    // ---- store phase: element (m, k) of the tile
-    for (uint32_t e = tid; e < kMatRows * S; e += kMatThreads) {
-      if constexpr (MODE == kModeInner) {
-        const uint32_t k = e / kMatRows, m = e % kMatRows;
-        const uint64_t d = d0 + m;
-        if (d < a.num_sub) {
-          const uint64_t q = d & mp_mask, o = d >> a.log_mp;
-          const uint64_t pos = q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS));
-          uint32_t v[8];
-          tile_load(v, reinterpret_cast<const uint4 *>(sA), m * S + k);
-          if (a.post) post_mul<F>(v, a.post, pos);
-          fe_store_global(a.dst, pos, v);
-        }
-      } else {
-        const uint32_t m = e / S, k = e % S;
-        const uint64_t d = d0 + m;
-        if (d < a.num_sub) {
-          const uint64_t rev = reverse_digits(a, d);
-          uint32_t v[8];
-          tile_load(v, reinterpret_cast<const uint4 *>(sA), m * S + k);
-          if (a.post) post_mul<F>(v, a.post, (rev << LOGS) | k);
-          fe_store_global(a.dst, (rev << LOGS) | k, v);
+        if (live) {
+#pragma unroll
+          for (int h = 0; h < 32; ++h) r[h] = __float_as_uint(__uint_as_float(r[h]) + 12582912.0f);
+          uint32_t z[9];
+          byte_merge(z, r, ma.off[k]);
+          uint32_t y[8];
+          mont_mul_z9<F>(y, z, t);
+          fe_store_global(a.dst, pos, y);
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acc_empty[buf]);
     }
-    __syncthreads();
+  }
+
+  // ---------------------------------------------------------- teardown
+  // Every copy into shared memory and every MMA must be complete before the
+  // shared memory and TMEM go away.  Normally these waits return at once;
+  // after an abort they are bounded like every other wait.
+  __syncthreads();
+  if (tid == 0) {
+    const uint64_t t0 = mat_global_ns();
+    while (!mbar_try(&bar_e, 0) && mat_global_ns() - t0 < ma.wait_ns) {
+    }
+    // last use u of each staging slot s: completion #u has parity u & 1
+    for (uint64_t s = 0; s < (uint64_t)kMatRing && s < loads_issued; ++s) {
+      const uint64_t u = (loads_issued - 1 - s) / kMatRing;
+      while (!mbar_try(&stage_full[s], (uint32_t)(u & 1)) && mat_global_ns() - t0 < ma.wait_ns) {
+      }
+    }
+  }
+  if (tid == 32) {
+    // a commit tracks every MMA this thread issued before it
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(&bar_done))
+                 : "memory");
+    const uint64_t t0 = mat_global_ns();
+    while (!mbar_try(&bar_done, 0) && mat_global_ns() - t0 < ma.wait_ns) {
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(TMEM_COLS));
   }
-}
-
-template <int LOGS>
-constexpr int matrix_smem_bytes() {
-  return (32 << LOGS) * (32 << LOGS) * 2 + kMatRows * (32 << LOGS) * 2;
 }
 
 }  // namespace gb300ntt

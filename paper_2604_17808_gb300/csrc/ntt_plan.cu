@@ -27,6 +27,7 @@
 #include "ntt_launch.h"
 #include "ntt_matrix.cuh"
 #include "ntt_plan.h"
+#include "nvtx_range.h"
 
 using namespace gb300ntt;
 
@@ -330,6 +331,7 @@ ntt_status check_buffer(const void *ptr) {
 extern "C" {
 
 ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int coset) {
+  NvtxRange range("ntt_plan_create");
   if (!out) return NTT_ERR_INVALID_ARG;
   *out = nullptr;
   if (field != NTT_FIELD_BLS12_381_FR && field != NTT_FIELD_BN254_FR) return NTT_ERR_INVALID_ARG;
@@ -401,6 +403,7 @@ ntt_status ntt_plan_set_coset_shift(ntt_plan plan, const uint64_t shift[4]) {
   const cudaError_t e = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   if (r == NTT_OK) r = cuda_status(e);
+  if (r == NTT_OK) r = matrix_build_coset(plan);
   return r;
 }
 
@@ -417,6 +420,7 @@ ntt_status ntt_plan_destroy(ntt_plan plan) {
 }
 
 ntt_status ntt_execute(ntt_plan plan, ntt_kind kind, const void *d_in, void *d_out, ntt_stream stream) {
+  NvtxRange range("ntt_execute");
   if (!plan) return NTT_ERR_INVALID_ARG;
   if (!kind_is_valid((int)kind, plan->has_coset)) return NTT_ERR_INVALID_ARG;
   NTT_TRY(check_buffer(d_in));

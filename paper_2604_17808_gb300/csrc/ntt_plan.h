@@ -60,12 +60,16 @@ struct ntt_plan_s {
 namespace gb300ntt {
 
 // Resources of the matrix-form path (ntt_matrix.cu): a nested plan with
-// passes of at most 2^3 points and the byte matrices E per pass size.
+// passes of at most 2^3 points, the byte matrices E (fp16, B-operand
+// layout) of its passes and their ByteMerge offsets.
 struct MatrixResources {
   ntt_plan nested = nullptr;
-  uint4 *e[2][4] = {};      // [direction][log S] E matrices, B-operand layout
-  uint32_t *err = nullptr;  // device error word of matrix launches
-  uint32_t offset[9] = {};  // 2^18 * p
+  uint4 *e_inner[2][4] = {};        // [direction][log S]: DFT matrix of passes >= 1
+  uint32_t off_inner[2][4][8][8] = {};
+  uint4 *e_first[3] = {};           // [table kind]: pass 0, its factors folded in
+  uint32_t off_first[3][8][8] = {};
+  uint32_t one[8] = {};             // 2^256 mod p
+  uint32_t *err = nullptr;          // device error word of matrix launches
 };
 
 std::vector<uint32_t> split_passes(uint32_t log_n);
@@ -90,6 +94,7 @@ void release_plan_tables(ntt_plan p);
 // matrix (tensor-core) path, ntt_matrix.cu
 bool matrix_path_available(ntt_plan p);
 ntt_status prepare_matrix_path(ntt_plan p);
+ntt_status matrix_build_coset(ntt_plan p);  // after a coset-shift change
 ntt_status matrix_poll_error(ntt_plan p, uint32_t *code);
 ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st);
 uint32_t matrix_launches(ntt_plan p);

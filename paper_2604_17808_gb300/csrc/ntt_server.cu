@@ -31,6 +31,7 @@
 
 #include "ntt_launch.h"
 #include "ntt_plan.h"
+#include "nvtx_range.h"
 
 using namespace gb300ntt;
 
@@ -162,6 +163,7 @@ void CUDART_CB slot_done(void *arg) {
 
 // Dispatch the admitted requests (up to the batch limits) on slot `sl`.
 void dispatch(ntt_server_s *s, Slot *sl) {
+  NvtxRange range("ntt_server_dispatch");
   std::vector<BatchJobRef> jobs;
   uint64_t elems = 0;
   sl->tickets.clear();

@@ -26,6 +26,7 @@
 
 #include "ntt_launch.h"
 #include "ntt_plan.h"
+#include "nvtx_range.h"
 
 using namespace gb300ntt;
 
@@ -165,6 +166,7 @@ ntt_status tune_apply(ntt_plan p, const TuneChoice &c) {
 }  // namespace gb300ntt
 
 extern "C" ntt_status ntt_plan_autotune(ntt_plan plan, uint32_t reps, ntt_tune_result *result) {
+  NvtxRange range("ntt_plan_autotune");
   if (!plan) return NTT_ERR_INVALID_ARG;
   if (reps == 0) reps = 3;
   const uint32_t log_n = plan->log_n;

@@ -151,3 +151,43 @@ def test_bounded_wait_times_out_and_reports():
         N.ntt_batch_debug_stall(False)
         N.ntt_batch_set_wait_limit(2_000_000_000)
         N.ntt_plan_destroy(plan)
+
+
+def test_batch_autotune_keeps_results_and_runs_matrix_plans():
+    """ntt_batch_autotune picks a policy (persistent kernel, or the larger jobs
+    as ordinary transforms on parallel graph branches); whatever it picks,
+    every output must stay bit-exact with the oracle digests, and lists with
+    the same signature (other buffers) follow the policy.  Jobs whose plan is
+    on the matrix path run inside the batch's graph as ordinary transforms."""
+    with open(os.path.join(HERE, "golden", "oracle_digests.json")) as fh:
+        g = json.load(fh)["batched"]
+    sizes = batch_sizes(64, 14, 22, config_seed(4))
+    plans = {ln: N.ntt_plan_create("bls12_381_fr", ln) for ln in sorted(set(sizes))}
+    try:
+        N.ntt_plan_set_path(plans[20], "matrix")   # one size on the tensor-core path
+        ins, outs, jobs = [], [], []
+        for j, ln in enumerate(sizes):
+            x = dev(uniform_elements("bls12_381_fr", 1 << ln, config_seed(4, j)))
+            y = torch.empty_like(x)
+            ins.append(x)
+            outs.append(y)
+            jobs.append((plans[ln], "forward", x, y))
+        res = N.ntt_batch_autotune(jobs, reps=1)
+        assert res["candidates"] >= 2 and res["best_ms"] > 0
+        assert res["best_ms"] <= min(res["persistent_ms"], res["loop_ms"]) * 1.05 + 0.05
+        for y in outs:
+            y.zero_()
+        N.ntt_batch_submit(jobs)
+        for j, job in enumerate(g["jobs"]):
+            assert digest(host(outs[j])) == job["output_sha256"], j
+        # same signature, other output buffers: the tuned policy applies
+        outs2 = [torch.empty_like(x) for x in ins]
+        N.ntt_batch_submit([(plans[ln], "forward", x, y) for ln, x, y in zip(sizes, ins, outs2)])
+        for j, job in enumerate(g["jobs"]):
+            assert digest(host(outs2[j])) == job["output_sha256"], j
+        assert N.ntt_batch_poll_error() == 0
+        assert N.ntt_plan_poll_error(plans[20]) == 0
+    finally:
+        N.ntt_batch_cache_clear()
+        for p in plans.values():
+            N.ntt_plan_destroy(p)
