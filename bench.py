@@ -696,30 +696,31 @@ def measure_modmul(torch, N, stream, count: int = 1 << 22, reps: int = 64) -> di
     return res
 
 
-def measure_batched(torch, N, stream, reps: int) -> dict:
+def measure_batched(torch, N, stream, reps: int, tune: bool = True) -> dict:
     """64 BLS12-381 forward jobs, log2 n uniform on {14..22} (seeded): one
-    persistent launch replayed from a CUDA graph vs one transform per call."""
+    transform per call (the loop) against the batched forms -- every job in
+    one persistent launch replayed from a CUDA graph (untuned), and the form
+    ntt_batch_autotune picks after ntt_plan_autotune has tuned each size's
+    plan (tuned).  All forms must give identical outputs."""
     from ntt_synth import batch_sizes
 
     sizes = batch_sizes(64, 14, 22, config_seed(4))
     plans = {ln: N.ntt_plan_create(FIELD, ln) for ln in sorted(set(sizes))}
     try:
         xs = [to_dev(torch, uniform_elements(FIELD, 1 << ln, config_seed(4, j))) for j, ln in enumerate(sizes)]
-        ys = [torch.empty_like(x) for x in xs]
-        zs = [torch.empty_like(x) for x in xs]
-        jobs = [(plans[ln], "forward", x, y) for ln, x, y in zip(sizes, xs, ys)]
+        outs = {name: [torch.empty_like(x) for x in xs] for name in ("loop", "untuned", "tuned", "loop_tuned")}
         total = sum(1 << ln for ln in sizes)
 
-        def loop():
-            for ln, x, z in zip(sizes, xs, zs):
-                N.ntt_forward(plans[ln], x, z, stream)
+        def jobs(name):
+            return [(plans[ln], "forward", x, y) for ln, x, y in zip(sizes, xs, outs[name])]
 
-        N.ntt_batch_submit(jobs, stream)   # builds and captures the graph
-        loop()
-        torch.cuda.synchronize()
-        res = {}
-        for name, fn in (("batched", lambda: N.ntt_batch_submit(jobs, stream)), ("loop", loop)):
+        def loop(name):
+            for ln, x, y in zip(sizes, xs, outs[name]):
+                N.ntt_forward(plans[ln], x, y, stream)
+
+        def timed(fn) -> float:
             fn()
+            torch.cuda.synchronize()
             start = torch.cuda.Event(enable_timing=True)
             stop = torch.cuda.Event(enable_timing=True)
             start.record(stream)
@@ -727,16 +728,37 @@ def measure_batched(torch, N, stream, reps: int) -> dict:
                 fn()
             stop.record(stream)
             stop.synchronize()
-            res[name] = start.elapsed_time(stop) / reps
-        same = all(bool(torch.equal(y, z)) for y, z in zip(ys, zs))
+            return start.elapsed_time(stop) / reps
+
+        res = {"loop": timed(lambda: loop("loop")),
+               "untuned": timed(lambda: N.ntt_batch_submit(jobs("untuned"), stream))}
+        tuned_info = None
+        if tune:
+            t0 = time.perf_counter()
+            plan_choice = {ln: N.ntt_plan_autotune(p, reps=2) for ln, p in plans.items()}
+            tuned_info = N.ntt_batch_autotune(jobs("tuned"), reps=2)
+            tuned_info["tuning_s"] = round(time.perf_counter() - t0, 2)
+            tuned_info["plans"] = {str(ln): {"path": c["path"], "pass_log": c["pass_log"], "tile_log": c["tile_log"]}
+                                   for ln, c in plan_choice.items()}
+            res["tuned"] = timed(lambda: N.ntt_batch_submit(jobs("tuned"), stream))
+            res["loop_tuned"] = timed(lambda: loop("loop_tuned"))
+        names = [n for n in ("loop", "untuned", "tuned", "loop_tuned") if n in res]
+        same = all(bool(torch.equal(a, b)) for n in names[1:] for a, b in zip(outs["loop"], outs[n]))
         err = N.ntt_batch_poll_error()
-        return {"workload": "64 BLS12-381 forward NTTs, log2 n uniform on {14..22}, "
-                            f"{total} elements", "batched_ms": round(res["batched"], 4),
-                "loop_ms": round(res["loop"], 4),
-                "batched_elements_per_s": total / (res["batched"] * 1e-3),
-                "loop_elements_per_s": total / (res["loop"] * 1e-3),
-                "speedup": round(res["loop"] / res["batched"], 3),
-                "identical_results": same, "device_error": err}
+        out = {"workload": "64 BLS12-381 forward NTTs, log2 n uniform on {14..22}, " f"{total} elements",
+               "loop_ms": round(res["loop"], 4), "batched_ms": round(res["untuned"], 4),
+               "batched_elements_per_s": total / (res["untuned"] * 1e-3),
+               "loop_elements_per_s": total / (res["loop"] * 1e-3),
+               "speedup": round(res["loop"] / res["untuned"], 3),
+               "identical_results": same, "device_error": err}
+        if tune:
+            out.update({"tuned_batched_ms": round(res["tuned"], 4),
+                        "tuned_batched_elements_per_s": total / (res["tuned"] * 1e-3),
+                        "loop_tuned_plans_ms": round(res["loop_tuned"], 4),
+                        "tuned_speedup_vs_loop": round(res["loop"] / res["tuned"], 3),
+                        "tuned_speedup_vs_loop_tuned_plans": round(res["loop_tuned"] / res["tuned"], 3),
+                        "tuning": tuned_info})
+        return out
     finally:
         N.ntt_batch_cache_clear()
         for p in plans.values():

@@ -67,17 +67,21 @@ U256 times_pow2(const HostField &F, U256 v, unsigned e) {
   return v;
 }
 
-// E[(k,h),(n,b)] = digit h of V[n][k] 2^(8b) 2^32 mod p, fp16, in the
-// K-major B-operand layout (N = K = 32 S), and the merge offsets
-// O_k = 2^32 C sum_n V[n][k] - B sum_h 2^(8h) mod p, C = 128 sum_b 2^(8b),
-// B = 0x4B400000 (the fp32 pattern of 1.5 2^23 in every accumulator).
-void build_e16(const HostField &F, uint32_t logs, const std::vector<U256> &V, std::vector<uint8_t> *e,
+// E[(k,h),(n,b)] = digit h of V[n][k] 2^(8b) g mod p, fp16, in the K-major
+// B-operand layout (N = K = 32 S), and the merge offsets
+// O_k = g C sum_n V[n][k] - B sum_h 2^(8h) mod p, C = 128 sum_b 2^(8b),
+// B = 0x4B400000 (the fp32 pattern of 1.5 2^23 in every accumulator), with
+// g = 2^32 for passes whose epilogue is the 9-row Montgomery product (its
+// 2^-288 leaves 2^-32 after the table's 2^256) and g = 1 for a last pass
+// reduced by Barrett.
+void build_e16(const HostField &F, uint32_t logs, const std::vector<U256> &V, bool scaled, std::vector<uint8_t> *e,
                uint32_t off[8][8]) {
   const uint32_t S = 1u << logs, K = 32 * S;
+  const unsigned gexp = scaled ? 32 : 0;
   e->assign((size_t)K * K * 2, 0);
   for (uint32_t n = 0; n < S; ++n) {
     for (uint32_t k = 0; k < S; ++k) {
-      U256 wv = times_pow2(F, V[(size_t)n * S + k], 32);
+      U256 wv = times_pow2(F, V[(size_t)n * S + k], gexp);
       for (uint32_t b = 0; b < 32; ++b) {
         int dg[32];
         balanced_digits(wv, dg);
@@ -100,7 +104,7 @@ void build_e16(const HostField &F, uint32_t logs, const std::vector<U256> &V, st
   for (uint32_t k = 0; k < S; ++k) {
     U256 colsum = u256(0);
     for (uint32_t n = 0; n < S; ++n) colsum = F.add(colsum, V[(size_t)n * S + k]);
-    const U256 corr = times_pow2(F, F.mul(c, colsum), 32);
+    const U256 corr = times_pow2(F, F.mul(c, colsum), gexp);
     const U256 o = F.sub(corr, bsig);
     for (int i = 0; i < 4; ++i) {
       off[k][2 * i] = (uint32_t)o.w[i];
@@ -117,6 +121,21 @@ ntt_status upload(ntt_plan p, const std::vector<uint8_t> &buf, uint4 **out) {
   ntt_status s = cuda_status(cudaMalloc(out, buf.size()));
   if (s == NTT_OK) s = cuda_status(cudaMemcpy(*out, buf.data(), buf.size(), cudaMemcpyHostToDevice));
   return s;
+}
+
+// floor(2^288 / p) by binary long division (the quotient has 34 bits).
+uint64_t barrett_mu(const HostField &F) {
+  U256 r = u256(0);
+  uint64_t q = 0;
+  for (int i = 288; i >= 0; --i) {
+    r = u256_add_raw(r, r);   // r < p < 2^255: no overflow
+    if (i == 288) r = u256_add_raw(r, u256(1));
+    if (u256_geq(r, F.p)) {
+      r = u256_sub_raw(r, F.p);
+      if (i < 64) q |= 1ull << i;
+    }
+  }
+  return q;
 }
 
 // Pass-0 factors pre_n of table kind tk for the nested plan q (empty: all 1).
@@ -147,11 +166,13 @@ void release_matrix_resources(ntt_plan p) {
   MatrixResources *m = p->matrix;
   if (!m) return;
   if (m->nested) ntt_plan_destroy(m->nested);
-  for (auto &row : m->e_inner)
-    for (uint4 *q : row)
+  for (auto &dir : m->e_inner)
+    for (auto &lg : dir)
+      for (uint4 *q : lg)
+        if (q) cudaFree(q);
+  for (auto &tk : m->e_first)
+    for (uint4 *q : tk)
       if (q) cudaFree(q);
-  for (uint4 *q : m->e_first)
-    if (q) cudaFree(q);
   if (m->err) cudaFree(m->err);
   delete m;
   p->matrix = nullptr;
@@ -165,8 +186,9 @@ ntt_status matrix_build_coset(ntt_plan p) {
   ntt_plan q = m->nested;
   std::vector<uint8_t> buf;
   const std::vector<U256> V = pass_matrix(F, q->pass_log[0], false, pass0_factors(F, q, kCoset));
-  build_e16(F, q->pass_log[0], V, &buf, m->off_first[kCoset]);
-  return upload(p, buf, &m->e_first[kCoset]);
+  const int sc = q->num_passes > 1 ? 1 : 0;   // a single pass of a coset forward ends in Barrett
+  build_e16(F, q->pass_log[0], V, sc == 1, &buf, m->off_first[kCoset][sc]);
+  return upload(p, buf, &m->e_first[kCoset][sc]);
 }
 
 static ntt_status ensure_matrix(ntt_plan p) {
@@ -198,26 +220,36 @@ static ntt_status ensure_matrix(ntt_plan p) {
   if (s != NTT_OK) return s;
   const HostField F = host_field(p->field);
   std::vector<uint8_t> buf;
-  // inner passes: plain DFT matrices per direction and size
-  for (uint32_t j = 1; j < q->num_passes; ++j) {
+  const uint32_t P = q->num_passes;
+  // Matrices needed: [scaled] = the pass ends in the 9-row Montgomery product
+  // (every pass but the last, and the last pass of a coset inverse, whose
+  // factor is s^-n); unscaled = a last pass reduced by Barrett.
+  auto need = [&](ntt_status *st, uint4 **slot, uint32_t logs, bool inverse, const std::vector<U256> &pre,
+                  bool scaled, uint32_t off[8][8]) {
+    if (*st != NTT_OK || *slot) return;
+    build_e16(F, logs, pass_matrix(F, logs, inverse, pre), scaled, &buf, off);
+    *st = upload(p, buf, slot);
+    if (*st == NTT_OK) p->device_bytes += buf.size();
+  };
+  for (uint32_t j = 1; j < P; ++j) {
     const uint32_t logs = q->pass_log[j];
     for (int dir = 0; dir < 2; ++dir) {
-      if (m->e_inner[dir][logs]) continue;
-      build_e16(F, logs, pass_matrix(F, logs, dir == 1, {}), &buf, m->off_inner[dir][logs]);
-      s = upload(p, buf, &m->e_inner[dir][logs]);
-      if (s != NTT_OK) return s;
-      p->device_bytes += buf.size();
+      const bool last = j == P - 1;
+      if (!last || (dir == 1 && p->has_coset))
+        need(&s, &m->e_inner[dir][logs][1], logs, dir == 1, {}, true, m->off_inner[dir][logs][1]);
+      if (last) need(&s, &m->e_inner[dir][logs][0], logs, dir == 1, {}, false, m->off_inner[dir][logs][0]);
     }
   }
-  // pass 0: one matrix per table kind, its factors folded in
   for (int tk = kForward; tk <= kCoset; ++tk) {
     if (tk == kCoset && !p->has_coset) continue;
-    const std::vector<U256> V = pass_matrix(F, q->pass_log[0], tk == kInverse, pass0_factors(F, q, tk));
-    build_e16(F, q->pass_log[0], V, &buf, m->off_first[tk]);
-    s = upload(p, buf, &m->e_first[tk]);
-    if (s != NTT_OK) return s;
-    p->device_bytes += buf.size();
+    const std::vector<U256> pre = pass0_factors(F, q, tk);
+    const uint32_t logs = q->pass_log[0];
+    if (P > 1 || (tk == kInverse && p->has_coset))
+      need(&s, &m->e_first[tk][1], logs, tk == kInverse, pre, true, m->off_first[tk][1]);
+    if (P == 1) need(&s, &m->e_first[tk][0], logs, tk == kInverse, pre, false, m->off_first[tk][0]);
   }
+  if (s != NTT_OK) return s;
+  m->mu = barrett_mu(F);
   const U256 one = F.to_mont(u256(1));
   for (int i = 0; i < 4; ++i) {
     m->one[2 * i] = (uint32_t)one.w[i];
@@ -253,22 +285,28 @@ ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *
   const int tk = table_kind(kind);
   const int dir = tk == kInverse ? 1 : 0;
   uint32_t log_m = 0;
-  for (uint32_t j = 0; j < q->num_passes; ++j) {
+  const uint32_t P = q->num_passes;
+  for (uint32_t j = 0; j < P; ++j) {
     MatrixPassArgs ma{};
     int mode = 0;
     build_pass_args(q, kind, in, out, j, &ma.a, &mode);
     const uint32_t logs = q->pass_log[j];
     log_m += logs;
+    // the last pass without output factors ends in a Barrett reduction
+    const bool barrett = j == P - 1 && !ma.a.post;
+    const int sc = barrett ? 0 : 1;
     if (j == 0) {
-      ma.e = m->e_first[tk];
-      std::memcpy(ma.off, m->off_first[tk], sizeof ma.off);
+      ma.e = m->e_first[tk][sc];
+      std::memcpy(ma.off, m->off_first[tk][sc], sizeof ma.off);
       mode = kModeFirst;   // the pass-0 factors are in E
     } else {
-      ma.e = m->e_inner[dir][logs];
-      std::memcpy(ma.off, m->off_inner[dir][logs], sizeof ma.off);
+      ma.e = m->e_inner[dir][logs][sc];
+      std::memcpy(ma.off, m->off_inner[dir][logs][sc], sizeof ma.off);
     }
+    ma.barrett = barrett ? 1u : 0u;
+    ma.mu = m->mu;
     if (!ma.e) return NTT_ERR_UNSUPPORTED;
-    if (j + 1 < q->num_passes) {
+    if (j + 1 < P) {
       ma.next = q->tw[tk][j + 1];
       ma.next_log = log_m + q->pass_log[j + 1];
     }

@@ -26,12 +26,14 @@
 // element per pass, nothing else on the integer multiply pipe.
 //
 // Exactness: |a E| <= 2^14 and K = 32 S <= 256 terms keep every partial sum
-// within 2^22, exact in fp16 x fp16 -> fp32 accumulation; fp16 holds the byte
-// digits exactly (integers up to 2^11).  With |acc| <= 2^22, acc + 1.5 2^23
-// lies in [2^23, 2^24), so its fp32 bit pattern is 0x4B400000 + acc exactly
-// (one FADD, no float-to-integer conversion).  Z < 2^31 2^248 (256/255) + p <
-// 2^280, so the 9-row Montgomery product (R = 2^288) of Z and T < p ends below
-// 2p and one conditional subtraction makes it canonical.
+// within 2^22; fp16 holds the byte digits exactly (integers up to 2^11).
+// Each accumulator starts at the bias 1.5 * 2^23 (written into TMEM by the
+// epilogue), so every running value the tensor core forms is an integer in
+// [2^23, 2^24], exact in fp32, and the final fp32 bit pattern is 0x4B400000
+// + acc: the accumulators are read as integers with no conversion at all.
+// Z < 2^31 2^248 (256/255) + p < 2^280, so the 9-row Montgomery product (R =
+// 2^288) of Z and T < p ends below 2p and one conditional subtraction makes
+// it canonical; the last pass (no factor) uses a Barrett reduction instead.
 //
 // Kernel structure (persistent, one CTA per SM, warp-specialised):
 //   warp 0       TMA loader: cp.async.bulk of each chunk's inputs (128 rows
@@ -39,12 +41,14 @@
 //                loads E (resident for the whole kernel);
 //   warp 1       MMA issuer: two tcgen05.mma (K = 16 each) per chunk into a
 //                double-buffered TMEM accumulator (N = 32 S columns each);
-//   warps 2-5    digit converters: staging element -> 32 fp16 digits by byte
+//   warps 2-3    digit converters: staging element -> 32 fp16 digits by byte
 //                permutes (0x64 | byte = 1024 + byte as fp16) and one packed
-//                fp16 subtraction, written as the A operand chunk;
-//   warps 6-21   epilogue: tcgen05.ld of one output's 32 accumulators,
-//                ByteMerge by funnel shifts and carry chains, the Montgomery
-//                product with T, store.
+//                fp16 subtraction, written as the A operand chunk (two rows
+//                per thread);
+//   warps 4-19   epilogue: tcgen05.ld of one output's 32 accumulators (and
+//                tcgen05.st of the bias back into them for the buffer's next
+//                tile), ByteMerge by funnel shifts and carry chains, the
+//                Montgomery product with T (or Barrett), store.
 // Every wait is an mbarrier wait bounded by %globaltimer; on timeout the CTA
 // records NTT_ERR_TIMEOUT, every role stops, copies in flight are waited for
 // (bounded) and TMEM is freed before the kernel returns.
@@ -59,10 +63,12 @@
 namespace gb300ntt {
 
 constexpr int kMatRows = 128;                 // sub-transforms per tile (MMA M)
-constexpr int kMatConvWarps = 4;              // one converter thread per tile row
+constexpr int kMatConvWarps = 2;              // each converter thread takes two tile rows
 constexpr int kMatEpiWarps = 16;              // four per TMEM lane quarter
 constexpr int kMatFirstEpiWarp = 2 + kMatConvWarps;
-constexpr int kMatThreads = 32 * (kMatFirstEpiWarp + kMatEpiWarps);   // 704
+// 20 warps: five per SM sub-partition, so up to 102 registers per thread
+// fit its 16K-entry register file (22 warps would cap them at 80)
+constexpr int kMatThreads = 32 * (kMatFirstEpiWarp + kMatEpiWarps);   // 640
 constexpr int kMatRing = 8;                   // chunks in flight (A operand and staging)
 constexpr uint32_t kMatChunkBytes = kMatRows * 32 * 2;   // A chunk: 128 rows x 32 fp16 digits
 constexpr uint32_t kMatStageBytes = kMatRows * 32;       // staging: 128 elements
@@ -76,6 +82,8 @@ struct MatrixPassArgs {
   uint32_t next_log;
   uint32_t off[8][8];     // O_k (canonical), k < S
   uint32_t one[8];        // 2^256 mod p: the factor when no table applies
+  uint32_t barrett;       // 1: no factor, E without the 2^32 (last pass): Barrett reduction
+  uint64_t mu;            // floor(2^288 / p)
   uint32_t *err;          // device error word
   uint64_t wait_ns;       // bound of every wait
 };
@@ -129,6 +137,19 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
   return done != 0;
 }
 
+// The same test, but the thread may sleep in hardware (up to about 0.1 ms)
+// until the phase completes, instead of issuing instructions while it polls.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(100000u)
+      : "memory");
+  return done != 0;
+}
+
 // Wait for completion of the phase of `bar` with the given parity, bounded
 // by wait_ns; gives up early when another role has aborted.  On timeout the
 // CTA's abort flag and the device error word are set.
@@ -137,7 +158,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const 
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = mat_global_ns();
   for (;;) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try_sleep(bar, parity)) return true;
     if (*abort) return false;
     if (mat_global_ns() - t0 > ma.wait_ns) {
       *abort = 1;
@@ -170,6 +191,17 @@ __device__ __forceinline__ void digits_f16(uint32_t w[16], const uint32_t x[8]) 
     asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * i]) : "r"(lo), "r"(k1152));
     asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * i + 1]) : "r"(hi), "r"(k1152));
   }
+}
+
+// Write the bias 1.5 * 2^23 (fp32 bits 0x4B400000) into 32 consecutive TMEM
+// columns of this warp's 32 lanes: accumulating on top of it, every MMA
+// result is already the pattern 0x4B400000 + acc (see the header).
+__device__ __forceinline__ void tmem_store_bias(uint32_t taddr) {
+  const uint32_t b = kMatFp32Magic;
+#pragma unroll
+  for (uint32_t c = 0; c < 32; c += 8)
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr + c), "r"(b)
+                 : "memory");
 }
 
 // Z = sum_h u_h 2^(8h) + off, u_h = fp32 bits of acc_h + 1.5 2^23 (< 2^31).
@@ -253,6 +285,32 @@ __device__ __forceinline__ void mont_mul_z9(uint32_t r[8], const uint32_t z[9], 
     acc[8] = 0;
   }
   reduce_once<F>(r, acc);
+}
+
+// r = z mod p, canonical, for z < 2^280 (nine limbs): q = floor(floor(z /
+// 2^224) mu / 2^64) with mu = floor(2^288 / p) is floor(z / p) or one less
+// (the truncations lose less than 2^-30 + 2^-8), so z - q p lies in [0, 2p)
+// and one conditional subtraction finishes.  q < 2^27.
+template <class F>
+__device__ __forceinline__ void barrett_z9(uint32_t r[8], const uint32_t z[9], uint64_t mu) {
+  const uint64_t zt = ((uint64_t)z[8] << 32) | z[7];
+  const uint32_t q = (uint32_t)__umul64hi(zt, mu);
+  uint32_t qp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  row_even_p<F>(qp, q);
+  row_odd_p<F>(qp, q);
+  uint32_t d[8];
+  asm("sub.cc.u32  %0, %8,  %16;\n\t"
+      "subc.cc.u32 %1, %9,  %17;\n\t"
+      "subc.cc.u32 %2, %10, %18;\n\t"
+      "subc.cc.u32 %3, %11, %19;\n\t"
+      "subc.cc.u32 %4, %12, %20;\n\t"
+      "subc.cc.u32 %5, %13, %21;\n\t"
+      "subc.cc.u32 %6, %14, %22;\n\t"
+      "subc.u32    %7, %15, %23;"
+      : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7])
+      : "r"(z[0]), "r"(z[1]), "r"(z[2]), "r"(z[3]), "r"(z[4]), "r"(z[5]), "r"(z[6]), "r"(z[7]), "r"(qp[0]),
+        "r"(qp[1]), "r"(qp[2]), "r"(qp[3]), "r"(qp[4]), "r"(qp[5]), "r"(qp[6]), "r"(qp[7]));
+  reduce_once<F>(r, d);
 }
 
 // Position of input n (or, for inner passes, output n) of sub-transform d.
@@ -341,33 +399,42 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   uint64_t loads_issued = 0;   // (loader thread) stage uses, for the teardown
   if (warp == 0) {
     // ------------------------------------------------------ TMA loader
+    // The whole warp loops; lane 0 waits and posts the byte count, then the
+    // lanes issue the chunk's contiguous runs between them (passes whose
+    // sub-transform stride Mp is below 128 have 128 / Mp runs per chunk).
     if (lane == 0) {
       mbar_expect_tx(&bar_e, E_BYTES);
       for (uint32_t off = 0; off < E_BYTES; off += 16384u) {
         const uint32_t bytes = E_BYTES - off < 16384u ? E_BYTES - off : 16384u;
         bulk_g2s(sE + off, reinterpret_cast<const uint8_t *>(ma.e) + off, bytes, &bar_e);
       }
-      uint64_t g = 0;
-      for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
-        const uint64_t d0 = (blockIdx.x + it * gridDim.x) * kMatRows;
-        const uint64_t rest = a.num_sub - d0;
-        const uint32_t valid = rest < (uint64_t)kMatRows ? (uint32_t)rest : (uint32_t)kMatRows;
-        uint32_t run = valid;
-        if constexpr (MODE == kModeInner) {
-          const uint64_t mp = 1ull << a.log_mp;
-          if (mp < run) run = (uint32_t)mp;
-        }
-        for (uint32_t n = 0; n < S; ++n, ++g) {
-          const uint32_t s = (uint32_t)(g % kMatRing);
-          const uint64_t u = g / kMatRing;
-          if (u >= 1 && !mbar_wait(&stage_empty[s], (uint32_t)((u - 1) & 1), ma, abort)) break;
-          mbar_expect_tx(&stage_full[s], valid * 32u);
-          uint8_t *dst = sStage + s * kMatStageBytes;
-          for (uint32_t r0 = 0; r0 < valid; r0 += run)
-            bulk_g2s(dst + r0 * 32u, a.src + 2 * mat_in_pos<LOGS, MODE>(a, d0 + r0, n), run * 32u, &stage_full[s]);
-          loads_issued = g + 1;
-        }
+    }
+    uint64_t g = 0;
+    for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
+      const uint64_t d0 = (blockIdx.x + it * gridDim.x) * kMatRows;
+      const uint64_t rest = a.num_sub - d0;
+      const uint32_t valid = rest < (uint64_t)kMatRows ? (uint32_t)rest : (uint32_t)kMatRows;
+      uint32_t run = valid;
+      if constexpr (MODE == kModeInner) {
+        const uint64_t mp = 1ull << a.log_mp;
+        if (mp < run) run = (uint32_t)mp;
       }
+      bool ok = true;
+      for (uint32_t n = 0; n < S; ++n, ++g) {
+        const uint32_t s = (uint32_t)(g % kMatRing);
+        const uint64_t u = g / kMatRing;
+        if (lane == 0) {
+          ok = u == 0 || mbar_wait(&stage_empty[s], (uint32_t)((u - 1) & 1), ma, abort);
+          if (ok) mbar_expect_tx(&stage_full[s], valid * 32u);
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+        uint8_t *dst = sStage + s * kMatStageBytes;
+        for (uint32_t r0 = lane * run; r0 < valid; r0 += 32 * run)
+          bulk_g2s(dst + r0 * 32u, a.src + 2 * mat_in_pos<LOGS, MODE>(a, d0 + r0, n), run * 32u, &stage_full[s]);
+        if (lane == 0) loads_issued = g + 1;
+      }
+      if (!ok) break;
     }
   } else if (warp == 1) {
     // ------------------------------------------------------ MMA issuer
@@ -382,7 +449,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
       for (uint64_t it = 0; ok && it < my_tiles; ++it) {
         const uint32_t buf = (uint32_t)(it & 1);
         const uint64_t v = it >> 1;
-        if (v >= 1 && !mbar_wait(&acc_empty[buf], (uint32_t)((v - 1) & 1), ma, abort)) break;
+        if (!mbar_wait(&acc_empty[buf], (uint32_t)(v & 1), ma, abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dcol = taddr + buf * NC;
         for (uint32_t n = 0; n < S; ++n, ++g) {
@@ -397,7 +464,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
           for (uint32_t ks = 0; ks < 2; ++ks) {
             const uint64_t da = mat_desc(a_base + c * kMatChunkBytes + ks * 256, 128, 4 * 128);
             const uint64_t db = mat_desc(b_base + (2 * n + ks) * 256, 128, (K >> 3) * 128);
-            const uint32_t accum = (n | ks) ? 1u : 0u;
+            const uint32_t accum = 1u;   // on top of the bias the epilogue wrote
             asm volatile(
                 "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
@@ -415,7 +482,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
     }
   } else if (warp < kMatFirstEpiWarp) {
     // ------------------------------------------------------ digit converters
-    const uint32_t m = tid - 64;   // tile row
+    const uint32_t m0 = tid - 64;   // tile rows m0 and m0 + 64
     uint64_t g = 0;
     for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
       bool ok = true;
@@ -426,22 +493,30 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
           ok = false;
           break;
         }
-        const uint4 *st = reinterpret_cast<const uint4 *>(sStage + c * kMatStageBytes) + 2 * m;
-        const uint4 lo = st[0], hi = st[1];
+        const uint4 *st = reinterpret_cast<const uint4 *>(sStage + c * kMatStageBytes);
+        uint32_t w[2][16];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+          const uint32_t m = m0 + 64 * rr;
+          const uint4 lo = st[2 * m], hi = st[2 * m + 1];
+          const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+          digits_f16(w[rr], x);
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&stage_empty[c]);
-        const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-        uint32_t w[16];
-        digits_f16(w, x);
         if (u >= 1 && !mbar_wait(&chunk_empty[c], (uint32_t)((u - 1) & 1), ma, abort)) {
           ok = false;
           break;
         }
         uint8_t *dst = sA + c * kMatChunkBytes;
 #pragma unroll
-        for (uint32_t q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4 *>(dst + core_offset(m, 8 * q, 32)) =
-              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        for (int rr = 0; rr < 2; ++rr) {
+          const uint32_t m = m0 + 64 * rr;
+#pragma unroll
+          for (uint32_t q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4 *>(dst + core_offset(m, 8 * q, 32)) =
+                make_uint4(w[rr][4 * q], w[rr][4 * q + 1], w[rr][4 * q + 2], w[rr][4 * q + 3]);
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&chunk_full[c]);
       }
@@ -454,23 +529,43 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
     const uint32_t part = ew >> 2;                  // 0..3: outputs k = part, part + 4
     const uint32_t m = 32 * quarter + lane;
     const uint64_t next_mask = (1ull << ma.next_log) - 1;
+    const uint32_t lane_addr = taddr + ((32 * quarter) << 16);
+    for (uint32_t buf = 0; buf < 2; ++buf) {
+#pragma unroll
+      for (int o = 0; o < 2; ++o)
+        if (part + 4 * o < S) tmem_store_bias(lane_addr + buf * NC + 32 * (part + 4 * o));
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(&acc_empty[0]);
+    mbar_arrive(&acc_empty[1]);
     for (uint64_t it = 0; it < my_tiles; ++it) {
       const uint32_t buf = (uint32_t)(it & 1);
-      if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t d = (blockIdx.x + it * gridDim.x) * kMatRows + m;
       const bool live = d < a.num_sub;
-      for (uint32_t k = part; k < S; k += 4) {
-        const uint64_t pos = live ? mat_out_pos<LOGS, MODE>(a, d, k) : 0;
-        uint32_t t[8];
-        if (ma.post) {
-          if (live) fe_load_global(t, ma.post, pos);
-        } else if (ma.next) {
-          if (live) fe_load_global(t, ma.next, pos & next_mask);
-        } else {
+      // this thread's outputs k = part and part + 4: positions and factors
+      // are loaded before the accumulators are ready
+      uint64_t pos[2] = {0, 0};
+      uint32_t t[2][8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) t[j] = ma.one[j];
+      for (int o = 0; o < 2; ++o) {
+        const uint32_t k = part + 4 * o;
+        if (k < S && live) {
+          pos[o] = mat_out_pos<LOGS, MODE>(a, d, k);
+          if (ma.post) fe_load_global(t[o], ma.post, pos[o]);
+          else if (ma.next) fe_load_global(t[o], ma.next, pos[o] & next_mask);
         }
+        if (!ma.post && !ma.next) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[o][j] = ma.one[j];
+        }
+      }
+      if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int o = 0; o < 2; ++o) {
+        const uint32_t k = part + 4 * o;
+        if (k >= S) break;
         uint32_t r[32];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -480,18 +575,19 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
               "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
               "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
               "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr + ((32 * quarter) << 16) + buf * NC + 32 * k));
+            : "r"(lane_addr + buf * NC + 32 * k));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        tmem_store_bias(lane_addr + buf * NC + 32 * k);   // for this buffer's next tile
         if (live) {
-#pragma unroll
-          for (int h = 0; h < 32; ++h) r[h] = __float_as_uint(__uint_as_float(r[h]) + 12582912.0f);
           uint32_t z[9];
           byte_merge(z, r, ma.off[k]);
           uint32_t y[8];
-          mont_mul_z9<F>(y, z, t);
-          fe_store_global(a.dst, pos, y);
+          if (ma.barrett) barrett_z9<F>(y, z, ma.mu);
+          else mont_mul_z9<F>(y, z, t[o]);
+          fe_store_global(a.dst, pos[o], y);
         }
       }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&acc_empty[buf]);
     }

@@ -64,11 +64,14 @@ namespace gb300ntt {
 // layout) of its passes and their ByteMerge offsets.
 struct MatrixResources {
   ntt_plan nested = nullptr;
-  uint4 *e_inner[2][4] = {};        // [direction][log S]: DFT matrix of passes >= 1
-  uint32_t off_inner[2][4][8][8] = {};
-  uint4 *e_first[3] = {};           // [table kind]: pass 0, its factors folded in
-  uint32_t off_first[3][8][8] = {};
+  // [..][scaled]: scaled = 1 for passes ending in the 9-row Montgomery
+  // product (E carries 2^32), 0 for a last pass reduced by Barrett
+  uint4 *e_inner[2][4][2] = {};     // [direction][log S][scaled]: DFT matrix of passes >= 1
+  uint32_t off_inner[2][4][2][8][8] = {};
+  uint4 *e_first[3][2] = {};        // [table kind][scaled]: pass 0, its factors folded in
+  uint32_t off_first[3][2][8][8] = {};
   uint32_t one[8] = {};             // 2^256 mod p
+  uint64_t mu = 0;                  // floor(2^288 / p)
   uint32_t *err = nullptr;          // device error word of matrix launches
 };
 
