@@ -43,8 +43,8 @@
 //                double-buffered TMEM accumulator (N = 32 S columns each);
 //   warps 2-3    digit converters: staging element -> 32 fp16 digits by byte
 //                permutes (0x64 | byte = 1024 + byte as fp16) and one packed
-//                fp16 subtraction, written as the A operand chunk (two rows
-//                per thread);
+//                fp16 subtraction, written as the A operand chunk (the two
+//                warps take alternate chunks, four rows per thread);
 //   warps 4-19   epilogue: tcgen05.ld of one output's 32 accumulators (and
 //                tcgen05.st of the bias back into them for the buffer's next
 //                tile), ByteMerge by funnel shifts and carry chains, the
@@ -63,13 +63,17 @@
 namespace gb300ntt {
 
 constexpr int kMatRows = 128;                 // sub-transforms per tile (MMA M)
-constexpr int kMatConvWarps = 2;              // each converter thread takes two tile rows
+constexpr int kMatConvWarps = 2;              // alternate chunks; four tile rows per thread
 constexpr int kMatEpiWarps = 16;              // four per TMEM lane quarter
 constexpr int kMatFirstEpiWarp = 2 + kMatConvWarps;
 // 20 warps: five per SM sub-partition, so up to 102 registers per thread
 // fit its 16K-entry register file (22 warps would cap them at 80)
 constexpr int kMatThreads = 32 * (kMatFirstEpiWarp + kMatEpiWarps);   // 640
-constexpr int kMatRing = 8;                   // chunks in flight (A operand and staging)
+// Chunks in flight: the staging ring must cover the latency of the input
+// loads from HBM (16 x 4 KiB = two tiles ahead); the A-operand ring only the
+// hand-off from the converters to the MMA issuer within the SM.
+constexpr int kMatStageRing = 16;
+constexpr int kMatRing = 4;
 constexpr uint32_t kMatChunkBytes = kMatRows * 32 * 2;   // A chunk: 128 rows x 32 fp16 digits
 constexpr uint32_t kMatStageBytes = kMatRows * 32;       // staging: 128 elements
 constexpr uint32_t kMatFp32Magic = 0x4B400000u;          // bits of 1.5 * 2^23
@@ -338,7 +342,7 @@ __host__ __device__ constexpr uint32_t matrix_tmem_cols() {
 
 template <int LOGS>
 __host__ __device__ constexpr int matrix_smem_bytes() {
-  return (32 << LOGS) * (32 << LOGS) * 2 + kMatRing * (int)(kMatChunkBytes + kMatStageBytes);
+  return (32 << LOGS) * (32 << LOGS) * 2 + kMatRing * (int)kMatChunkBytes + kMatStageRing * (int)kMatStageBytes;
 }
 
 // One matrix pass (MODE: kModeInner or kModeFirst; pass-0 multipliers are
@@ -351,13 +355,14 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   constexpr uint32_t TMEM_COLS = matrix_tmem_cols<LOGS>();
   constexpr uint32_t E_BYTES = NC * K * 2;
   static_assert(NC <= 256 && NC % 16 == 0, "one MMA covers all outputs");
-  static_assert(matrix_smem_bytes<LOGS>() <= 227 * 1024 - 512, "shared memory");
+  static_assert(matrix_smem_bytes<LOGS>() <= 227 * 1024 - 1024, "shared memory");
+  static_assert(kMatRing % kMatConvWarps == 0 && kMatStageRing % kMatConvWarps == 0, "slots of one converter");
   extern __shared__ __align__(1024) uint8_t mat_smem[];
   uint8_t *sE = mat_smem;
   uint8_t *sA = mat_smem + E_BYTES;
   uint8_t *sStage = sA + kMatRing * kMatChunkBytes;
   __shared__ __align__(8) uint64_t bar_e;
-  __shared__ __align__(8) uint64_t stage_full[kMatRing], stage_empty[kMatRing];
+  __shared__ __align__(8) uint64_t stage_full[kMatStageRing], stage_empty[kMatStageRing];
   __shared__ __align__(8) uint64_t chunk_full[kMatRing], chunk_empty[kMatRing];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ __align__(8) uint64_t bar_done;
@@ -372,10 +377,12 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
 
   if (tid == 0) {
     mbar_init(&bar_e, 1);
-    for (int i = 0; i < kMatRing; ++i) {
+    for (int i = 0; i < kMatStageRing; ++i) {
       mbar_init(&stage_full[i], 1);
-      mbar_init(&stage_empty[i], 32 * kMatConvWarps);
-      mbar_init(&chunk_full[i], 32 * kMatConvWarps);
+      mbar_init(&stage_empty[i], 32);   // the converter warp of the chunk
+    }
+    for (int i = 0; i < kMatRing; ++i) {
+      mbar_init(&chunk_full[i], 32);
       mbar_init(&chunk_empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -421,8 +428,8 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
       }
       bool ok = true;
       for (uint32_t n = 0; n < S; ++n, ++g) {
-        const uint32_t s = (uint32_t)(g % kMatRing);
-        const uint64_t u = g / kMatRing;
+        const uint32_t s = (uint32_t)(g % kMatStageRing);
+        const uint64_t u = g / kMatStageRing;
         if (lane == 0) {
           ok = u == 0 || mbar_wait(&stage_empty[s], (uint32_t)((u - 1) & 1), ma, abort);
           if (ok) mbar_expect_tx(&stage_full[s], valid * 32u);
@@ -482,45 +489,35 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
     }
   } else if (warp < kMatFirstEpiWarp) {
     // ------------------------------------------------------ digit converters
-    const uint32_t m0 = tid - 64;   // tile rows m0 and m0 + 64
-    uint64_t g = 0;
-    for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
-      bool ok = true;
-      for (uint32_t n = 0; n < S; ++n, ++g) {
-        const uint32_t c = (uint32_t)(g % kMatRing);
-        const uint64_t u = g / kMatRing;
-        if (!mbar_wait(&stage_full[c], (uint32_t)(u & 1), ma, abort)) {
-          ok = false;
-          break;
-        }
-        const uint4 *st = reinterpret_cast<const uint4 *>(sStage + c * kMatStageBytes);
-        uint32_t w[2][16];
+    // Converter warp cw takes the chunks g = cw, cw + 2, ... (ring slots of
+    // one parity: both ring sizes are even), each thread the rows lane,
+    // lane + 32, lane + 64, lane + 96.
+    const uint32_t cw = warp - 2;
+    const uint64_t chunks = my_tiles * S;
+    for (uint64_t g = cw; g < chunks && !*abort; g += kMatConvWarps) {
+      const uint32_t sl = (uint32_t)(g % kMatStageRing);
+      const uint64_t us = g / kMatStageRing;
+      const uint32_t c = (uint32_t)(g % kMatRing);
+      const uint64_t u = g / kMatRing;
+      if (!mbar_wait(&stage_full[sl], (uint32_t)(us & 1), ma, abort)) break;
+      if (u >= 1 && !mbar_wait(&chunk_empty[c], (uint32_t)((u - 1) & 1), ma, abort)) break;
+      const uint4 *st = reinterpret_cast<const uint4 *>(sStage + sl * kMatStageBytes);
+      uint8_t *dst = sA + c * kMatChunkBytes;
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-          const uint32_t m = m0 + 64 * rr;
-          const uint4 lo = st[2 * m], hi = st[2 * m + 1];
-          const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-          digits_f16(w[rr], x);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&stage_empty[c]);
-        if (u >= 1 && !mbar_wait(&chunk_empty[c], (uint32_t)((u - 1) & 1), ma, abort)) {
-          ok = false;
-          break;
-        }
-        uint8_t *dst = sA + c * kMatChunkBytes;
+      for (uint32_t rr = 0; rr < 4; ++rr) {
+        const uint32_t m = lane + 32 * rr;
+        const uint4 lo = st[2 * m], hi = st[2 * m + 1];
+        const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        uint32_t w[16];
+        digits_f16(w, x);
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-          const uint32_t m = m0 + 64 * rr;
-#pragma unroll
-          for (uint32_t q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4 *>(dst + core_offset(m, 8 * q, 32)) =
-                make_uint4(w[rr][4 * q], w[rr][4 * q + 1], w[rr][4 * q + 2], w[rr][4 * q + 3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&chunk_full[c]);
+        for (uint32_t q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4 *>(dst + core_offset(m, 8 * q, 32)) =
+              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
       }
-      if (!ok) break;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&stage_empty[sl]);
+      mbar_arrive(&chunk_full[c]);
     }
   } else {
     // ------------------------------------------------------ epilogue
@@ -562,8 +559,12 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
       }
       if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // ByteMerge of each output (accumulators back to the bias as they are
+      // read), then the outputs' reductions side by side
+      uint32_t z[2][9];
+      constexpr int kOuts = S > 4 ? 2 : 1;
 #pragma unroll
-      for (int o = 0; o < 2; ++o) {
+      for (int o = 0; o < kOuts; ++o) {
         const uint32_t k = part + 4 * o;
         if (k >= S) break;
         uint32_t r[32];
@@ -578,14 +579,24 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
             : "r"(lane_addr + buf * NC + 32 * k));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         tmem_store_bias(lane_addr + buf * NC + 32 * k);   // for this buffer's next tile
-        if (live) {
-          uint32_t z[9];
-          byte_merge(z, r, ma.off[k]);
-          uint32_t y[8];
-          if (ma.barrett) barrett_z9<F>(y, z, ma.mu);
-          else mont_mul_z9<F>(y, z, t[o]);
-          fe_store_global(a.dst, pos[o], y);
+        byte_merge(z[o], r, ma.off[k]);
+      }
+      if (live && part < S) {
+        uint32_t y[2][8];
+        if (kOuts == 2) {
+          if (ma.barrett) {
+            barrett_z9<F>(y[0], z[0], ma.mu);
+            barrett_z9<F>(y[1], z[1], ma.mu);
+          } else {
+            mont_mul_z9<F>(y[0], z[0], t[0]);
+            mont_mul_z9<F>(y[1], z[1], t[1]);
+          }
+        } else {
+          if (ma.barrett) barrett_z9<F>(y[0], z[0], ma.mu);
+          else mont_mul_z9<F>(y[0], z[0], t[0]);
         }
+#pragma unroll
+        for (int o = 0; o < kOuts; ++o) fe_store_global(a.dst, pos[o], y[o]);
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -603,8 +614,8 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
     while (!mbar_try(&bar_e, 0) && mat_global_ns() - t0 < ma.wait_ns) {
     }
     // last use u of each staging slot s: completion #u has parity u & 1
-    for (uint64_t s = 0; s < (uint64_t)kMatRing && s < loads_issued; ++s) {
-      const uint64_t u = (loads_issued - 1 - s) / kMatRing;
+    for (uint64_t s = 0; s < (uint64_t)kMatStageRing && s < loads_issued; ++s) {
+      const uint64_t u = (loads_issued - 1 - s) / kMatStageRing;
       while (!mbar_try(&stage_full[s], (uint32_t)(u & 1)) && mat_global_ns() - t0 < ma.wait_ns) {
       }
     }
