@@ -577,6 +577,44 @@ def measure_matrix(torch, N, stream, bufs, steps: int, log_n: int) -> dict:
         N.ntt_plan_destroy(plan)
 
 
+def measure_paths(torch, N, stream, log_n: int, reps: int = 5) -> dict:
+    """Matrix (tensor-core) path against the butterfly path at one size,
+    BLS12-381 Fr: two untimed forward transforms per path (matrix first, so
+    a profiler can address its launches), then `reps` timed forward+inverse
+    pairs; outputs compared across paths and the round trip checked."""
+    x = to_dev(torch, uniform_elements(FIELD, 1 << log_n, config_seed(3, 100)))
+    plan = N.ntt_plan_create(FIELD, log_n)
+    out = {"workload": f"BLS12-381 Fr NTT n=2^{log_n}, forward and inverse, matrix vs butterfly path"}
+    ys = {}
+    try:
+        for path in ("matrix", "butterfly"):
+            N.ntt_plan_set_path(plan, path)
+            y = torch.empty_like(x)
+            z = torch.empty_like(x)
+            for _ in range(2):
+                N.ntt_forward(plan, x, y, stream)
+            torch.cuda.synchronize()
+            start = torch.cuda.Event(enable_timing=True)
+            stop = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            for _ in range(reps):
+                N.ntt_forward(plan, x, y, stream)
+                N.ntt_inverse(plan, y, z, stream)
+            stop.record(stream)
+            stop.synchronize()
+            ms = start.elapsed_time(stop) / (2 * reps)
+            ys[path] = y
+            out[path] = {"ms_per_transform": round(ms, 4), "elements_per_s": (1 << log_n) / (ms * 1e-3),
+                         "passes": N.ntt_plan_describe(plan)["launches_per_transform"],
+                         "round_trip_exact": bool(torch.equal(z, x))}
+        out["identical"] = bool(torch.equal(ys["matrix"], ys["butterfly"]))
+        out["matrix_vs_butterfly"] = round(out["butterfly"]["ms_per_transform"] / out["matrix"]["ms_per_transform"], 3)
+        out["device_error"] = N.ntt_plan_poll_error(plan)
+        return out
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
 def measure_quotient(torch, N, stream, reps: int, log_n: int = 20, blowup_log: int = 2) -> dict:
     """A prover's quotient step: coset NTTs of A, B, C (degree < 2n, zero
     padded) on the coset s<omega_m> of m = 4n points, the fused pointwise
@@ -1164,7 +1202,8 @@ def run_leg(args) -> None:
           "coset_2_24": lambda: measure_coset_2_24(torch, N, stream, steps=3),
           "wide": lambda: measure_wide(torch, N, stream, steps=10),
           "msm": lambda: measure_msm(torch, N, stream, reps=5, log_sizes=tuple(args.msm_log), curve=args.msm_curve),
-          "commit": lambda: measure_commit(torch, N, stream, reps=5)}[args.leg]
+          "commit": lambda: measure_commit(torch, N, stream, reps=5),
+          "paths": lambda: measure_paths(torch, N, stream, args.log_n)}[args.leg]
     print(json.dumps({args.leg: fn()}), flush=True)
 
 
@@ -1178,7 +1217,8 @@ def main() -> None:
     ap.add_argument("--quick", action="store_true", help="skip the 2^24 secondary measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true", help="run only the full serving sweep")
-    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide", "msm", "commit"],
+    ap.add_argument("--leg", choices=["modmul", "quotient", "batched", "n_2_28", "coset_2_24", "wide", "msm", "commit",
+                                      "paths"],
                     help="run only this secondary measurement and print its JSON (for profiling)")
     ap.add_argument("--msm-log", type=int, nargs="+", default=[22, 24, 26],
                     help="log2 point counts of the msm leg (default: the paper's 22 24 26)")

@@ -40,6 +40,23 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Launch with programmatic stream serialisation (see pdl_trigger_and_wait):
+// consecutive passes overlap their launch latency and CTA scheduling.
+template <class K, class A>
+cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, int smem, cudaStream_t st, const A &a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -103,12 +120,12 @@ cudaError_t pass_launch(int mode, const PassArgs &a, uint64_t tiles, cudaStream_
   const dim3 grid((unsigned)tiles), block(TileCfg<TL>::kThreads);
   const int smem = TileCfg<TL>::kBytes;
   switch (mode) {
-    case kModeInner: ntt_pass_kernel<F, LOGS, kModeInner, TL, FUSED><<<grid, block, smem, st>>>(a); break;
-    case kModeFirst: ntt_pass_kernel<F, LOGS, kModeFirst, TL, FUSED><<<grid, block, smem, st>>>(a); break;
-    case kModeFirstPre: ntt_pass_kernel<F, LOGS, kModeFirstPre, TL, FUSED><<<grid, block, smem, st>>>(a); break;
+    case kModeInner: return launch_pdl(ntt_pass_kernel<F, LOGS, kModeInner, TL, FUSED>, grid, block, smem, st, a);
+    case kModeFirst: return launch_pdl(ntt_pass_kernel<F, LOGS, kModeFirst, TL, FUSED>, grid, block, smem, st, a);
+    case kModeFirstPre:
+      return launch_pdl(ntt_pass_kernel<F, LOGS, kModeFirstPre, TL, FUSED>, grid, block, smem, st, a);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <int LOGS, int TL>
@@ -280,11 +297,10 @@ template <int LOGS>
 cudaError_t matrix_logs(int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
   const int smem = matrix_smem_bytes<LOGS>();
   switch (mode) {
-    case kModeInner: ntt_matrix_pass_kernel<F, LOGS, kModeInner><<<grid, kMatThreads, smem, st>>>(ma); break;
-    case kModeFirst: ntt_matrix_pass_kernel<F, LOGS, kModeFirst><<<grid, kMatThreads, smem, st>>>(ma); break;
+    case kModeInner: return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeInner>, grid, kMatThreads, smem, st, ma);
+    case kModeFirst: return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeFirst>, grid, kMatThreads, smem, st, ma);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace

@@ -404,18 +404,23 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   const uint32_t taddr = s_taddr;
 
   uint64_t loads_issued = 0;   // (loader thread) stage uses, for the teardown
+  // E and the factor tables are plan constants: E is requested before the
+  // wait for the previous launch (programmatic dependent launch), every
+  // access to the vector comes after it.
+  if (tid == 0) {
+    mbar_expect_tx(&bar_e, E_BYTES);
+    for (uint32_t off = 0; off < E_BYTES; off += 16384u) {
+      const uint32_t bytes = E_BYTES - off < 16384u ? E_BYTES - off : 16384u;
+      bulk_g2s(sE + off, reinterpret_cast<const uint8_t *>(ma.e) + off, bytes, &bar_e);
+    }
+  }
+  pdl_trigger_and_wait();
+
   if (warp == 0) {
     // ------------------------------------------------------ TMA loader
     // The whole warp loops; lane 0 waits and posts the byte count, then the
     // lanes issue the chunk's contiguous runs between them (passes whose
     // sub-transform stride Mp is below 128 have 128 / Mp runs per chunk).
-    if (lane == 0) {
-      mbar_expect_tx(&bar_e, E_BYTES);
-      for (uint32_t off = 0; off < E_BYTES; off += 16384u) {
-        const uint32_t bytes = E_BYTES - off < 16384u ? E_BYTES - off : 16384u;
-        bulk_g2s(sE + off, reinterpret_cast<const uint8_t *>(ma.e) + off, bytes, &bar_e);
-      }
-    }
     uint64_t g = 0;
     for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
       const uint64_t d0 = (blockIdx.x + it * gridDim.x) * kMatRows;

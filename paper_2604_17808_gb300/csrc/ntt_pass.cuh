@@ -526,10 +526,21 @@ __device__ __forceinline__ void pass_tile(const PassArgs &a, uint64_t tile, uint
 
 // ------------------------------------------------------------ pass kernel
 
+// Programmatic dependent launch (the passes are launched with it): the next
+// launch on the stream may start as soon as every CTA of this one has begun
+// (its CTAs take SM slots as ours retire), and each thread waits here until
+// the previous launch has completed and its memory is visible before it
+// touches the vector.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger_and_wait() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <class F, int LOGS, int MODE, int TL, bool FUSED>
 __global__ void __launch_bounds__(TileCfg<TL>::kThreads, TileCfg<TL>::kMinBlocks)
     ntt_pass_kernel(const PassArgs a) {
   extern __shared__ uint4 smem[];
+  pdl_trigger_and_wait();
   pass_tile<F, LOGS, MODE, false, TL, FUSED>(a, blockIdx.x, smem);
 }
 
