@@ -70,7 +70,8 @@ typedef enum ntt_status {
     NTT_ERR_CUDA = 4,
     NTT_ERR_TIMEOUT = 5,   /* a device-side bounded wait ran out */
     NTT_ERR_BUDGET = 6,    /* a memory budget would be exceeded */
-    NTT_ERR_NO_DEVICE = 7  /* no usable CUDA device of compute capability 10.3 */
+    NTT_ERR_NO_DEVICE = 7, /* no usable CUDA device of compute capability 10.3 */
+    NTT_ERR_BOUNDS = 8     /* debug builds (NTT_DEBUG): a kernel index fell outside its buffer */
 } ntt_status;
 
 typedef enum ntt_field {
@@ -361,9 +362,24 @@ ntt_status ntt_plan_read_timing(ntt_plan plan, double ms_per_pass[NTT_MAX_PASSES
 
 /*
  * Device-detected error of the plan's last transforms (0 = none), cleared on
- * read.  Synchronises the device.
+ * read.  Synchronises the device.  In a debug build of the library (compiled
+ * with NTT_DEBUG: every vector and table access of the butterfly pass
+ * kernels, single and batched, is checked against the extent the plan
+ * recorded for it, and an access out of range is skipped instead of made),
+ * a failed check reports NTT_ERR_BOUNDS here.  ntt_build_is_debug tells
+ * which build is loaded.
  */
 ntt_status ntt_plan_poll_error(ntt_plan plan, uint32_t *code);
+int ntt_build_is_debug(void);
+
+/*
+ * Test hook of debug builds: the next butterfly transform of this plan runs
+ * with the recorded vector extent halved, so that the bounds checks of its
+ * kernels fire on in-range accesses (which are then skipped: no access is
+ * ever made outside a buffer) and NTT_ERR_BOUNDS reaches
+ * ntt_plan_poll_error.  Release builds return NTT_ERR_UNSUPPORTED.
+ */
+ntt_status ntt_debug_shrink_next_extent(ntt_plan plan);
 
 /*
  * Serving runtime (continuous batching).  A server keeps plans with their

@@ -19,7 +19,7 @@ from . import _build
 NTT_OK = 0
 STATUS_NAMES = {
     0: "NTT_OK", 1: "NTT_ERR_INVALID_ARG", 2: "NTT_ERR_UNSUPPORTED", 3: "NTT_ERR_OOM",
-    4: "NTT_ERR_CUDA", 5: "NTT_ERR_TIMEOUT", 6: "NTT_ERR_BUDGET", 7: "NTT_ERR_NO_DEVICE",
+    4: "NTT_ERR_CUDA", 5: "NTT_ERR_TIMEOUT", 6: "NTT_ERR_BUDGET", 7: "NTT_ERR_NO_DEVICE", 8: "NTT_ERR_BOUNDS",
 }
 FIELD = {"bls12_381_fr": 0, "bn254_fr": 1, "w377": 2, "w753": 3}
 KIND = {"forward": 0, "inverse": 1, "coset": 2, "coset_inverse": 3}
@@ -103,6 +103,8 @@ _SIGS = {
     "ntt_plan_autotune": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(TuneResult)]),
     "ntt_plan_set_passes": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_U32), _U32]),
     "ntt_plan_poll_error": (ctypes.c_int, [_VP, ctypes.POINTER(_U32)]),
+    "ntt_build_is_debug": (ctypes.c_int, []),
+    "ntt_debug_shrink_next_extent": (ctypes.c_int, [_VP]),
     "ntt_batch_submit_static": (ctypes.c_int, [ctypes.POINTER(Job), ctypes.c_size_t, _VP, _VP]),
     "ntt_batch_poll_error": (ctypes.c_int, [ctypes.POINTER(_U32)]),
     "ntt_batch_set_wait_limit": (ctypes.c_int, [_U64]),
@@ -163,6 +165,18 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         fn.restype = res
         fn.argtypes = args
     _lib = lib
+    return lib
+
+
+def load_debug() -> ctypes.CDLL:
+    """Build if needed and load the NTT_DEBUG library (bounds-checked pass
+    kernels) as a separate handle with the same signatures; plans made with
+    it must be used with it only."""
+    lib = ctypes.CDLL(_build.build_debug())
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
     return lib
 
 

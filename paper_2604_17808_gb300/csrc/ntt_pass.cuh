@@ -99,7 +99,29 @@ struct PassArgs {
   uint32_t num_digits;   // first: P - 1 untransformed digits to reverse
   uint8_t digit_log[kMaxPasses];    // first: log2 S_j of digit j (j = 1..P-1) at index j-1
   uint8_t digit_shift[kMaxPasses];  // first: log2(S_1 ... S_{j-1}) at index j-1
+  uint64_t n_vec;        // elements of src, dst and post (debug bounds checks)
+  uint64_t n_mul;        // entries of mul (debug bounds checks)
+  uint32_t *dbg_err;     // device error word the debug checks report to
 };
+
+// Debug builds (NTT_DEBUG): an index is checked against the extent recorded
+// for its buffer; out of range, NTT_ERR_BOUNDS goes to the plan's error word
+// and the access is skipped (no trap: the context stays usable).  Release
+// builds compile the checks away.
+#ifdef NTT_DEBUG
+__device__ __forceinline__ bool dbg_in(const PassArgs &a, uint64_t idx, uint64_t n) {
+  if (idx < n) return true;
+  if (a.dbg_err) atomicCAS(a.dbg_err, 0u, 8u /* NTT_ERR_BOUNDS */);
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_in(const PassArgs &, uint64_t, uint64_t) { return true; }
+#endif
+
+__device__ __forceinline__ void fe_zero(uint32_t r[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = 0;
+}
 
 // Output row of pass 0 for untransformed digits d (their significance reversed).
 __device__ __forceinline__ uint64_t reverse_digits(const PassArgs &a, uint64_t d) {
@@ -292,16 +314,22 @@ __device__ __forceinline__ void pass_tile_staged(const PassArgs &a, uint64_t til
       if constexpr (MODE == kModeInner) {
         const uint64_t q = d & mp_mask, o = d >> a.log_mp;
         const uint64_t pos = q + ((uint64_t)n << a.log_mp) + (o << (a.log_mp + LOGS));
-        if constexpr (CG) fe_load_global_cg(v, a.src, pos);
+        if (!dbg_in(a, pos, a.n_vec)) fe_zero(v);
+        else if constexpr (CG) fe_load_global_cg(v, a.src, pos);
         else fe_load_global(v, a.src, pos);
         uint32_t w[8];
-        fe_load_global(w, a.mul, ((uint64_t)n << a.log_mp) + q);
+        const uint64_t wi = ((uint64_t)n << a.log_mp) + q;
+        if (dbg_in(a, wi, a.n_mul)) fe_load_global(w, a.mul, wi);
+        else fe_zero(w);
         mont_mul<F>(v, v, w);
       } else {
-        fe_load_global(v, a.src, d + ((uint64_t)n << a.log_mp));
+        const uint64_t pos = d + ((uint64_t)n << a.log_mp);
+        if (dbg_in(a, pos, a.n_vec)) fe_load_global(v, a.src, pos);
+        else fe_zero(v);
         if constexpr (MODE == kModeFirstPre) {
           uint32_t w[8];
-          fe_load_global(w, a.mul, n);
+          if (dbg_in(a, n, a.n_mul)) fe_load_global(w, a.mul, n);
+          else fe_zero(w);
           mont_mul<F>(v, v, w);
         }
       }
@@ -339,8 +367,10 @@ __device__ __forceinline__ void pass_tile_staged(const PassArgs &a, uint64_t til
         const uint64_t pos = q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS));
         uint32_t v[8];
         tile_load(v, smem, (dl << LOGS) | bit_reverse_local<LOGS>(k));
-        if (a.post) post_mul<F>(v, a.post, pos);
-        fe_store_global(a.dst, pos, v);
+        if (dbg_in(a, pos, a.n_vec)) {
+          if (a.post) post_mul<F>(v, a.post, pos);
+          fe_store_global(a.dst, pos, v);
+        }
       }
     } else {
       const uint32_t dl = e >> LOGS, k = e & (S - 1);
@@ -349,8 +379,11 @@ __device__ __forceinline__ void pass_tile_staged(const PassArgs &a, uint64_t til
         const uint64_t rev = reverse_digits(a, d);
         uint32_t v[8];
         tile_load(v, smem, (dl << LOGS) | bit_reverse_local<LOGS>(k));
-        if (a.post) post_mul<F>(v, a.post, (rev << LOGS) | k);
-        fe_store_global(a.dst, (rev << LOGS) | k, v);
+        const uint64_t pos = (rev << LOGS) | k;
+        if (dbg_in(a, pos, a.n_vec)) {
+          if (a.post) post_mul<F>(v, a.post, pos);
+          fe_store_global(a.dst, pos, v);
+        }
       }
     }
   }
@@ -396,7 +429,8 @@ __device__ __forceinline__ void round_radix4_load(const PassArgs &a, uint64_t d0
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint64_t pos = elem_pos<LOGS, MODE>(a, d, low + j * Q);
-      if constexpr (CG) fe_load_global_cg(x[j], a.src, pos);
+      if (!dbg_in(a, pos, a.n_vec)) fe_zero(x[j]);
+      else if constexpr (CG) fe_load_global_cg(x[j], a.src, pos);
       else fe_load_global(x[j], a.src, pos);
     }
     if constexpr (MODE != kModeFirst) {
@@ -404,10 +438,9 @@ __device__ __forceinline__ void round_radix4_load(const PassArgs &a, uint64_t d0
       for (int j = 0; j < 4; ++j) {
         const uint32_t n = low + j * Q;
         uint32_t w[8];
-        if constexpr (MODE == kModeInner)
-          fe_load_global(w, a.mul, ((uint64_t)n << a.log_mp) + (d & ((1ull << a.log_mp) - 1)));
-        else
-          fe_load_global(w, a.mul, n);
+        const uint64_t wi = MODE == kModeInner ? ((uint64_t)n << a.log_mp) + (d & ((1ull << a.log_mp) - 1)) : n;
+        if (dbg_in(a, wi, a.n_mul)) fe_load_global(w, a.mul, wi);
+        else fe_zero(w);
         mont_mul<F>(x[j], x[j], w);
       }
     }
@@ -471,16 +504,19 @@ __device__ __forceinline__ void round_radix4_store(const PassArgs &a, uint64_t d
       }
       const uint64_t p0 = base + ((uint64_t)t << sh), p1 = base + ((uint64_t)(t + 2 * Q) << sh);
       const uint64_t p2 = base + ((uint64_t)(t + Q) << sh), p3 = base + ((uint64_t)(t + 3 * Q) << sh);
-      if (a.post) {   // output multipliers (uniform across the grid)
-        post_mul<F>(x0, a.post, p0);
-        post_mul<F>(x1, a.post, p1);
-        post_mul<F>(x2, a.post, p2);
-        post_mul<F>(x3, a.post, p3);
+      // (the four positions are checked through the larger of each pair)
+      if (dbg_in(a, p0 > p3 ? p0 : p3, a.n_vec) && dbg_in(a, p1 > p2 ? p1 : p2, a.n_vec)) {
+        if (a.post) {   // output multipliers (uniform across the grid)
+          post_mul<F>(x0, a.post, p0);
+          post_mul<F>(x1, a.post, p1);
+          post_mul<F>(x2, a.post, p2);
+          post_mul<F>(x3, a.post, p3);
+        }
+        fe_store_global(a.dst, p0, x0);
+        fe_store_global(a.dst, p1, x1);
+        fe_store_global(a.dst, p2, x2);
+        fe_store_global(a.dst, p3, x3);
       }
-      fe_store_global(a.dst, p0, x0);
-      fe_store_global(a.dst, p1, x1);
-      fe_store_global(a.dst, p2, x2);
-      fe_store_global(a.dst, p3, x3);
     }
   }
 }

@@ -268,6 +268,14 @@ void build_pass_args(ntt_plan p, int kind, const void *in, void *out, uint32_t j
     *mode = kModeInner;
   }
   if (kind == kCosetInverse && j == P - 1) a->post = p->post_coset_inv;
+  // extents for the bounds checks of debug builds
+  a->n_vec = 1ull << log_n;
+  if (j == 0) {
+    a->n_mul = a->mul ? (1ull << logs) : 0;
+  } else {
+    a->n_mul = 1ull << (a->log_mp + logs);
+  }
+  a->dbg_err = p->d_err;
 }
 
 // Tile structure of a pass: the fused tile when the pass is one wave of
@@ -281,10 +289,13 @@ bool use_fused_tile(ntt_plan p, uint32_t logs, uint32_t tl) {
 // Enqueue one transform: one kernel launch per pass.
 ntt_status enqueue_transform(ntt_plan p, int kind, const void *in, void *out, cudaStream_t st) {
   const FieldLaunchers &L = launchers(p->field);
+  const bool shrink = p->debug_shrink;   // debug-build test hook (see ntt_debug_shrink_next_extent)
+  p->debug_shrink = false;
   for (uint32_t j = 0; j < p->num_passes; ++j) {
     PassArgs a;
     int mode;
     build_pass_args(p, kind, in, out, j, &a, &mode);
+    if (shrink) a.n_vec >>= 1;
     const uint32_t logs = p->pass_log[j];
     cudaError_t e = timing_begin(p, (int)j, st);
     const uint32_t tl = p->pass_tl[j];
@@ -618,10 +629,29 @@ const char *ntt_status_string(ntt_status status) {
     case NTT_ERR_TIMEOUT: return "NTT_ERR_TIMEOUT";
     case NTT_ERR_BUDGET: return "NTT_ERR_BUDGET";
     case NTT_ERR_NO_DEVICE: return "NTT_ERR_NO_DEVICE";
+    case NTT_ERR_BOUNDS: return "NTT_ERR_BOUNDS";
   }
   return "NTT_ERR_UNKNOWN";
 }
 
 uint32_t ntt_version(void) { return 100; }
+
+int ntt_build_is_debug(void) {
+#ifdef NTT_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+ntt_status ntt_debug_shrink_next_extent(ntt_plan plan) {
+  if (!plan) return NTT_ERR_INVALID_ARG;
+#ifdef NTT_DEBUG
+  plan->debug_shrink = true;
+  return NTT_OK;
+#else
+  return NTT_ERR_UNSUPPORTED;
+#endif
+}
 
 }  // extern "C"

@@ -47,6 +47,7 @@ struct ntt_plan_s {
   uint4 *post_coset_inv = nullptr;  // s^-n, n < N: output multipliers of the coset inverse
   uint4 *scratch = nullptr;      // N elements (in-place transforms with > 1 pass)
   uint32_t *d_err = nullptr;     // device error word
+  bool debug_shrink = false;     // debug builds: next transform with its vector extent halved
   std::vector<void *> allocations;
   uint64_t device_bytes = 0;
   gb300ntt::MatrixResources *matrix = nullptr;
