@@ -163,8 +163,11 @@ ntt_status ntt_transform_host_async(ntt_plan plan, ntt_kind kind, const void *h_
 
 /*
  * Read back the plan's structure: number of passes, the log2 size of each
- * pass's sub-transforms (up to 4), and the number of kernel launches one
- * transform makes.
+ * pass's sub-transforms (up to 4), the number of kernel launches one
+ * transform makes and, on the matrix path, how many of its passes
+ * (passes 1 .. matrix_folded_passes) take their input factors folded into
+ * per-q byte matrices (so that the pass before them ends in a Barrett
+ * reduction instead of a Montgomery product).
  */
 /* Most passes a transform is split into (the matrix path splits 2^28 into
  * ten passes of at most 2^3 points). */
@@ -178,6 +181,8 @@ typedef struct ntt_plan_desc {
     uint32_t launches_per_transform;
     uint32_t path;
     uint64_t device_bytes;
+    uint32_t matrix_folded_passes;
+    uint32_t reserved;
 } ntt_plan_desc;
 ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out);
 

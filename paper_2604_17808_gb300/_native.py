@@ -41,6 +41,7 @@ class PlanDesc(ctypes.Structure):
         ("field", ctypes.c_uint32), ("log_n", ctypes.c_uint32), ("num_passes", ctypes.c_uint32),
         ("pass_log", ctypes.c_uint32 * MAX_PASSES), ("launches_per_transform", ctypes.c_uint32),
         ("path", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
+        ("matrix_folded_passes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -280,7 +281,7 @@ def ntt_plan_describe(plan: int) -> dict:
     _check(load().ntt_plan_describe(plan, ctypes.byref(d)), "ntt_plan_describe")
     return {"field": d.field, "log_n": d.log_n, "num_passes": d.num_passes,
             "pass_log": list(d.pass_log)[: d.num_passes], "launches_per_transform": d.launches_per_transform,
-            "path": d.path, "device_bytes": d.device_bytes}
+            "path": d.path, "device_bytes": d.device_bytes, "matrix_folded_passes": d.matrix_folded_passes}
 
 
 def ntt_plan_read_table(plan: int, kind, pass_index: int, table: int, first: int, count: int, h_out) -> None:

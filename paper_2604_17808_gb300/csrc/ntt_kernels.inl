@@ -23,7 +23,8 @@ cudaError_t pass11(int logs, int mode, bool fused, const PassArgs &a, uint64_t t
 cudaError_t prepare_batch();
 cudaError_t batch(const BatchLaunch &b, cudaStream_t st);
 cudaError_t prepare_matrix();
-cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st);
+cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, const CUtensorMap &in_map, uint32_t grid,
+                        cudaStream_t st);
 
 namespace {
 
@@ -42,8 +43,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Launch with programmatic stream serialisation (see pdl_trigger_and_wait):
 // consecutive passes overlap their launch latency and CTA scheduling.
-template <class K, class A>
-cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, int smem, cudaStream_t st, const A &a) {
+template <class K, class... A>
+cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, int smem, cudaStream_t st, const A &...a) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -54,7 +55,7 @@ cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, int smem, cudaStream_t s
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, a);
+  return cudaLaunchKernelEx(&cfg, kernel, a...);
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
@@ -294,22 +295,26 @@ cudaError_t set_matrix_attrs() {
 }
 
 template <int LOGS>
-cudaError_t matrix_logs(int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
+cudaError_t matrix_logs(int mode, const MatrixPassArgs &ma, const CUtensorMap &in_map, uint32_t grid,
+                        cudaStream_t st) {
   const int smem = matrix_smem_bytes<LOGS>();
   switch (mode) {
-    case kModeInner: return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeInner>, grid, kMatThreads, smem, st, ma);
-    case kModeFirst: return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeFirst>, grid, kMatThreads, smem, st, ma);
+    case kModeInner:
+      return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeInner>, grid, kMatThreads, smem, st, ma, in_map);
+    case kModeFirst:
+      return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeFirst>, grid, kMatThreads, smem, st, ma, in_map);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st) {
+cudaError_t matrix_pass(int logs, int mode, const MatrixPassArgs &ma, const CUtensorMap &in_map, uint32_t grid,
+                        cudaStream_t st) {
   switch (logs) {
-    case 1: return matrix_logs<1>(mode, ma, grid, st);
-    case 2: return matrix_logs<2>(mode, ma, grid, st);
-    case 3: return matrix_logs<3>(mode, ma, grid, st);
+    case 1: return matrix_logs<1>(mode, ma, in_map, grid, st);
+    case 2: return matrix_logs<2>(mode, ma, in_map, grid, st);
+    case 3: return matrix_logs<3>(mode, ma, in_map, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

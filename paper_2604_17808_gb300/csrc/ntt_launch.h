@@ -75,7 +75,8 @@ struct FieldLaunchers {
   cudaError_t (*mul_rep)(uint4 *out, const uint4 *a, const uint4 *b, uint64_t count, uint32_t reps, int variant,
                          cudaStream_t st);
   // one matrix-form pass (logs <= 3), `grid` persistent CTAs
-  cudaError_t (*matrix_pass)(int logs, int mode, const MatrixPassArgs &ma, uint32_t grid, cudaStream_t st);
+  cudaError_t (*matrix_pass)(int logs, int mode, const MatrixPassArgs &ma, const CUtensorMap &in_map, uint32_t grid,
+                             cudaStream_t st);
   // out[i] = (a[i] b[i] - c[i]) z[i mod z_len] (z given as z 2^512 mod M)
   cudaError_t (*quotient)(uint4 *out, const uint4 *a, const uint4 *b, const uint4 *c, const QuotientZ &z,
                           uint64_t count, cudaStream_t st);

@@ -35,10 +35,17 @@
 // 2^288) of Z and T < p ends below 2p and one conditional subtraction makes
 // it canonical; the last pass (no factor) uses a Barrett reduction instead.
 //
+// Folded passes (early passes: few q, many rows each): the rows d = q + o Mp
+// of a tile share q, and the pass's own input factors c(q, n) are folded
+// into E_q (V[n,k] c(q, n) in place of V[n,k]) with per-q offsets; the pass
+// before needs no factor and ends in Barrett.
+//
 // Kernel structure (persistent, one CTA per SM, warp-specialised):
-//   warp 0       TMA loader: cp.async.bulk of each chunk's inputs (128 rows
-//                of one input n, contiguous runs) into a staging ring; also
-//                loads E (resident for the whole kernel);
+//   warp 0       TMA loader: one tensor-map copy (cp.async.bulk.tensor) per
+//                chunk -- the 128 rows of one input n of a tile, whatever
+//                their stride -- into a staging ring; also loads E (E_q of
+//                a folded pass, again whenever q changes, once the MMAs
+//                reading the previous one are complete);
 //   warp 1       MMA issuer: two tcgen05.mma (K = 16 each) per chunk into a
 //                double-buffered TMEM accumulator (N = 32 S columns each);
 //   warps 2-3    digit converters: staging element -> 32 fp16 digits by byte
@@ -53,6 +60,8 @@
 // records NTT_ERR_TIMEOUT, every role stops, copies in flight are waited for
 // (bounded) and TMEM is freed before the kernel returns.
 #pragma once
+
+#include <cuda.h>   // CUtensorMap (the kernel's TMA descriptor parameter)
 
 #include <cstdint>
 
@@ -86,8 +95,19 @@ struct MatrixPassArgs {
   uint32_t next_log;
   uint32_t off[8][8];     // O_k (canonical), k < S
   uint32_t one[8];        // 2^256 mod p: the factor when no table applies
-  uint32_t barrett;       // 1: no factor, E without the 2^32 (last pass): Barrett reduction
+  uint32_t barrett;       // 1: no factor, E without the 2^32: Barrett reduction
   uint64_t mu;            // floor(2^288 / p)
+  // Folded passes: all 128 rows of a tile share the index q (d = q + o Mp,
+  // 128 consecutive o), so the pass's own input factors, which depend on
+  // (q, n) only, are folded into a per-q matrix E_q (e: Mp matrices of E
+  // bytes each) with per-q merge offsets (off_fold: S x 8 words per q).
+  // The CTAs work in groups of fold_group: CTA i of a group takes q = i
+  // (mod fold_group) of the same o blocks at the same time, so the group's
+  // 32-byte rows of neighbouring q meet in L2 as whole lines.
+  uint32_t fold;
+  uint32_t fold_group;
+  uint32_t tiles_per_q_log;   // log2 of the 128-row blocks of o per q
+  const uint32_t *off_fold;
   uint32_t *err;          // device error word
   uint64_t wait_ns;       // bound of every wait
 };
@@ -179,6 +199,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                    smem_addr(dst)),
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
+}
+
+// Tensor-map (TMA) load of a 4-D box into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // 32 fp16 digits (byte - 128) of one element, packed in 16 words: word 2i
@@ -348,7 +378,8 @@ __host__ __device__ constexpr int matrix_smem_bytes() {
 // One matrix pass (MODE: kModeInner or kModeFirst; pass-0 multipliers are
 // folded into E).
 template <class F, int LOGS, int MODE>
-__global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const MatrixPassArgs ma) {
+__global__ void __launch_bounds__(kMatThreads, 1)
+    ntt_matrix_pass_kernel(const MatrixPassArgs ma, const __grid_constant__ CUtensorMap in_map) {
   constexpr uint32_t S = 1u << LOGS;
   constexpr uint32_t K = 32 * S;                  // (n, b)
   constexpr uint32_t NC = 32 * S;                 // (k, h)
@@ -365,15 +396,34 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   __shared__ __align__(8) uint64_t stage_full[kMatStageRing], stage_empty[kMatStageRing];
   __shared__ __align__(8) uint64_t chunk_full[kMatRing], chunk_empty[kMatRing];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
-  __shared__ __align__(8) uint64_t bar_done;
+  __shared__ __align__(8) uint64_t bar_done, bar_efree;
   __shared__ uint32_t s_taddr;
   __shared__ int s_abort;
   volatile int *abort = &s_abort;
   const PassArgs &a = ma.a;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint64_t num_tiles = (a.num_sub + kMatRows - 1) / kMatRows;
-  // tiles of this CTA
-  const uint64_t my_tiles = blockIdx.x < num_tiles ? (num_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // Work units: tiles (128 consecutive rows d) of the plain pass; for a
+  // folded pass (q group, o block) pairs of the CTA's group.  Each CTA takes
+  // a contiguous range of units, so a folded pass changes q, and reloads E,
+  // only a few times per CTA.
+  const uint32_t groups = ma.fold ? gridDim.x / ma.fold_group : gridDim.x;
+  const uint32_t group = ma.fold ? blockIdx.x / ma.fold_group : blockIdx.x;
+  const uint32_t in_group = ma.fold ? blockIdx.x % ma.fold_group : 0;
+  const uint64_t num_units = ma.fold ? ((1ull << a.log_mp) / ma.fold_group) << ma.tiles_per_q_log
+                                     : (a.num_sub + kMatRows - 1) / kMatRows;
+  const uint64_t u_begin = group < groups ? num_units * group / groups : 0;
+  const uint64_t my_tiles = group < groups ? num_units * (group + 1) / groups - u_begin : 0;
+  const uint64_t mp_mask = (1ull << a.log_mp) - 1;
+  // q of unit u (folded passes), first row d of its tile and the step
+  // between the tile's rows (the rows are d0 + m * step, m < 128)
+  auto tile_q = [&](uint64_t u) -> uint64_t {
+    return ma.fold ? (u >> ma.tiles_per_q_log) * ma.fold_group + in_group : 0;
+  };
+  auto tile_d0 = [&](uint64_t u) -> uint64_t {
+    const uint64_t ob = u & ((1ull << ma.tiles_per_q_log) - 1);
+    return ma.fold ? tile_q(u) + ((ob * kMatRows) << a.log_mp) : u * kMatRows;
+  };
+  const uint64_t row_step = ma.fold ? (1ull << a.log_mp) : 1;
 
   if (tid == 0) {
     mbar_init(&bar_e, 1);
@@ -390,6 +440,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
       mbar_init(&acc_empty[i], 32 * kMatEpiWarps);
     }
     mbar_init(&bar_done, 1);
+    mbar_init(&bar_efree, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -404,49 +455,58 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   const uint32_t taddr = s_taddr;
 
   uint64_t loads_issued = 0;   // (loader thread) stage uses, for the teardown
-  // E and the factor tables are plan constants: E is requested before the
-  // wait for the previous launch (programmatic dependent launch), every
-  // access to the vector comes after it.
-  if (tid == 0) {
+  uint64_t e_issued = 0;       // (loader thread) E loads, for the teardown
+  // E (of a folded pass: E_q) into shared memory, completing on bar_e
+  auto load_e = [&](uint64_t q) {
+    const uint8_t *src = reinterpret_cast<const uint8_t *>(ma.e) + q * (uint64_t)E_BYTES;
     mbar_expect_tx(&bar_e, E_BYTES);
     for (uint32_t off = 0; off < E_BYTES; off += 16384u) {
       const uint32_t bytes = E_BYTES - off < 16384u ? E_BYTES - off : 16384u;
-      bulk_g2s(sE + off, reinterpret_cast<const uint8_t *>(ma.e) + off, bytes, &bar_e);
+      bulk_g2s(sE + off, src + off, bytes, &bar_e);
     }
+  };
+  // E and the factor tables are plan constants: the first E is requested
+  // before the wait for the previous launch (programmatic dependent launch),
+  // every access to the vector comes after it.
+  if (tid == 0 && my_tiles) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+    load_e(tile_q(u_begin));
+    e_issued = 1;
   }
   pdl_trigger_and_wait();
 
   if (warp == 0) {
     // ------------------------------------------------------ TMA loader
-    // The whole warp loops; lane 0 waits and posts the byte count, then the
-    // lanes issue the chunk's contiguous runs between them (passes whose
-    // sub-transform stride Mp is below 128 have 128 / Mp runs per chunk).
-    uint64_t g = 0;
-    for (uint64_t it = 0; it < my_tiles && !*abort; ++it) {
-      const uint64_t d0 = (blockIdx.x + it * gridDim.x) * kMatRows;
-      const uint64_t rest = a.num_sub - d0;
-      const uint32_t valid = rest < (uint64_t)kMatRows ? (uint32_t)rest : (uint32_t)kMatRows;
-      uint32_t run = valid;
-      if constexpr (MODE == kModeInner) {
-        const uint64_t mp = 1ull << a.log_mp;
-        if (mp < run) run = (uint32_t)mp;
-      }
+    // Lane 0: one tensor-map copy per chunk (the 128 rows of input n of the
+    // tile, whatever their stride in memory) into the staging ring; for a
+    // folded pass, E_q again whenever q changes, once the MMAs that read the
+    // previous E are done.
+    if (lane == 0) {
+      const uint32_t chunk_bytes = (uint32_t)(a.num_sub < (uint64_t)kMatRows ? a.num_sub : kMatRows) * 32u;
+      uint64_t g = 0;
       bool ok = true;
-      for (uint32_t n = 0; n < S; ++n, ++g) {
-        const uint32_t s = (uint32_t)(g % kMatStageRing);
-        const uint64_t u = g / kMatStageRing;
-        if (lane == 0) {
-          ok = u == 0 || mbar_wait(&stage_empty[s], (uint32_t)((u - 1) & 1), ma, abort);
-          if (ok) mbar_expect_tx(&stage_full[s], valid * 32u);
+      for (uint64_t it = 0; ok && it < my_tiles && !*abort; ++it) {
+        const uint64_t t = u_begin + it;
+        if (it > 0 && ma.fold && tile_q(t) != tile_q(t - 1)) {
+          ok = mbar_wait(&bar_efree, (uint32_t)((e_issued - 1) & 1), ma, abort);
+          if (!ok) break;
+          load_e(tile_q(t));
+          ++e_issued;
         }
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-        if (!ok) break;
-        uint8_t *dst = sStage + s * kMatStageBytes;
-        for (uint32_t r0 = lane * run; r0 < valid; r0 += 32 * run)
-          bulk_g2s(dst + r0 * 32u, a.src + 2 * mat_in_pos<LOGS, MODE>(a, d0 + r0, n), run * 32u, &stage_full[s]);
-        if (lane == 0) loads_issued = g + 1;
+        const uint64_t d0 = tile_d0(t);
+        const int c1 = (int)(d0 & mp_mask), c3 = (int)(d0 >> a.log_mp);
+        for (uint32_t n = 0; n < S; ++n, ++g) {
+          const uint32_t s = (uint32_t)(g % kMatStageRing);
+          const uint64_t u = g / kMatStageRing;
+          if (u >= 1 && !mbar_wait(&stage_empty[s], (uint32_t)((u - 1) & 1), ma, abort)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&stage_full[s], chunk_bytes);
+          tma_load_4d(sStage + s * kMatStageBytes, &in_map, 0, c1, (int)n, c3, &stage_full[s]);
+          loads_issued = g + 1;
+        }
       }
-      if (!ok) break;
     }
   } else if (warp == 1) {
     // ------------------------------------------------------ MMA issuer
@@ -454,11 +514,17 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
       // fp32 accumulate (bit 4), fp16 A and B (formats 0), K-major both,
       // N >> 3 at bit 17, M >> 4 at bit 24
       constexpr uint32_t idesc = (1u << 4) | ((NC >> 3) << 17) | ((uint32_t)(kMatRows >> 4) << 24);
-      bool ok = mbar_wait(&bar_e, 0, ma, abort);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      bool ok = true;
+      uint64_t e_used = 0;   // E loads consumed
       const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sE);
       uint64_t g = 0;
       for (uint64_t it = 0; ok && it < my_tiles; ++it) {
+        const uint64_t t = u_begin + it;
+        if (it == 0 || (ma.fold && tile_q(t) != tile_q(t - 1))) {
+          if (!mbar_wait(&bar_e, (uint32_t)(e_used & 1), ma, abort)) break;
+          ++e_used;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
         const uint32_t buf = (uint32_t)(it & 1);
         const uint64_t v = it >> 1;
         if (!mbar_wait(&acc_empty[buf], (uint32_t)(v & 1), ma, abort)) break;
@@ -490,6 +556,11 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_addr(&acc_full[buf]))
                      : "memory");
+        // the last tile of a q: E may be replaced once these MMAs are done
+        if (ma.fold && it + 1 < my_tiles && tile_q(t + 1) != tile_q(t))
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_addr(&bar_efree))
+                       : "memory");
       }
     }
   } else if (warp < kMatFirstEpiWarp) {
@@ -543,23 +614,27 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
     mbar_arrive(&acc_empty[1]);
     for (uint64_t it = 0; it < my_tiles; ++it) {
       const uint32_t buf = (uint32_t)(it & 1);
-      const uint64_t d = (blockIdx.x + it * gridDim.x) * kMatRows + m;
-      const bool live = d < a.num_sub;
+      const uint64_t u = u_begin + it;
+      const uint64_t d = tile_d0(u) + m * row_step;
+      const bool live = ma.fold || d < a.num_sub;
       // this thread's outputs k = part and part + 4: positions and factors
-      // are loaded before the accumulators are ready
+      // are loaded before the accumulators are ready; a folded pass ending
+      // in Barrett needs no factor and preloads its merge offsets instead
       uint64_t pos[2] = {0, 0};
-      uint32_t t[2][8];
+      uint32_t fac[2][8];
+      const uint4 *offq = reinterpret_cast<const uint4 *>(ma.off_fold + tile_q(u) * S * 8);   // S entries of q
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         const uint32_t k = part + 4 * o;
         if (k < S && live) {
           pos[o] = mat_out_pos<LOGS, MODE>(a, d, k);
-          if (ma.post) fe_load_global(t[o], ma.post, pos[o]);
-          else if (ma.next) fe_load_global(t[o], ma.next, pos[o] & next_mask);
+          if (ma.fold && ma.barrett) fe_load_global(fac[o], offq, k);
+          else if (ma.post) fe_load_global(fac[o], ma.post, pos[o]);
+          else if (ma.next) fe_load_global(fac[o], ma.next, pos[o] & next_mask);
         }
-        if (!ma.post && !ma.next) {
+        if (!ma.post && !ma.next && !ma.fold) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) t[o][j] = ma.one[j];
+          for (int j = 0; j < 8; ++j) fac[o][j] = ma.one[j];
         }
       }
       if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
@@ -584,7 +659,15 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
             : "r"(lane_addr + buf * NC + 32 * k));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         tmem_store_bias(lane_addr + buf * NC + 32 * k);   // for this buffer's next tile
-        byte_merge(z[o], r, ma.off[k]);
+        if (ma.fold && ma.barrett) {
+          byte_merge(z[o], r, fac[o]);
+        } else if (ma.fold) {
+          uint32_t off[8];
+          fe_load_global(off, offq, k);
+          byte_merge(z[o], r, off);
+        } else {
+          byte_merge(z[o], r, ma.off[k]);
+        }
       }
       if (live && part < S) {
         uint32_t y[2][8];
@@ -593,12 +676,12 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
             barrett_z9<F>(y[0], z[0], ma.mu);
             barrett_z9<F>(y[1], z[1], ma.mu);
           } else {
-            mont_mul_z9<F>(y[0], z[0], t[0]);
-            mont_mul_z9<F>(y[1], z[1], t[1]);
+            mont_mul_z9<F>(y[0], z[0], fac[0]);
+            mont_mul_z9<F>(y[1], z[1], fac[1]);
           }
         } else {
           if (ma.barrett) barrett_z9<F>(y[0], z[0], ma.mu);
-          else mont_mul_z9<F>(y[0], z[0], t[0]);
+          else mont_mul_z9<F>(y[0], z[0], fac[0]);
         }
 #pragma unroll
         for (int o = 0; o < kOuts; ++o) fe_store_global(a.dst, pos[o], y[o]);
@@ -616,7 +699,7 @@ __global__ void __launch_bounds__(kMatThreads, 1) ntt_matrix_pass_kernel(const M
   __syncthreads();
   if (tid == 0) {
     const uint64_t t0 = mat_global_ns();
-    while (!mbar_try(&bar_e, 0) && mat_global_ns() - t0 < ma.wait_ns) {
+    while (e_issued && !mbar_try(&bar_e, (uint32_t)((e_issued - 1) & 1)) && mat_global_ns() - t0 < ma.wait_ns) {
     }
     // last use u of each staging slot s: completion #u has parity u & 1
     for (uint64_t s = 0; s < (uint64_t)kMatStageRing && s < loads_issued; ++s) {

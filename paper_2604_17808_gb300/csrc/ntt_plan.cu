@@ -488,6 +488,7 @@ ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out) {
   out->launches_per_transform = plan->path == NTT_PATH_MATRIX ? matrix_launches(plan) : plan->launches;
   out->path = (uint32_t)plan->path;
   out->device_bytes = plan->device_bytes;
+  out->matrix_folded_passes = plan->path == NTT_PATH_MATRIX && plan->matrix ? plan->matrix->fold : 0;
   return NTT_OK;
 }
 

@@ -71,6 +71,11 @@ struct MatrixResources {
   uint32_t off_inner[2][4][2][8][8] = {};
   uint4 *e_first[3][2] = {};        // [table kind][scaled]: pass 0, its factors folded in
   uint32_t off_first[3][2][8][8] = {};
+  // Folded passes 1..fold: all 128 rows of a tile share q, and the pass's
+  // input factors c(q, n) are folded into one matrix E_q per q
+  uint32_t fold = 0;
+  uint4 *e_fold[3][kMaxPasses] = {};       // [table kind][pass]: Mp matrices E_q
+  uint32_t *off_fold[3][kMaxPasses] = {};  // [table kind][pass]: Mp x S offsets (8 words each)
   uint32_t one[8] = {};             // 2^256 mod p
   uint64_t mu = 0;                  // floor(2^288 / p)
   uint32_t *err = nullptr;          // device error word of matrix launches

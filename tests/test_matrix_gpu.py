@@ -86,6 +86,55 @@ def test_matrix_path_adversarial_inputs(field):
         N.ntt_plan_destroy(plan)
 
 
+# Folded passes: pass j >= 1 (not the last) is folded when each q has at
+# least 2^11 rows, i.e. log_n >= (points of passes 0..j, log2) + 11.  With
+# passes of 2^3 points: 2^17 and 2^18 fold pass 1, 2^20 passes 1-2, 2^24
+# passes 1-3.
+FOLDED = {17: 1, 18: 1, 20: 2, 24: 3}
+
+
+@pytest.mark.parametrize("field", FIELDS)
+@pytest.mark.parametrize("log_n", [17, 18, 20])
+def test_matrix_folded_passes_all_kinds(field, log_n):
+    # every kind, element by element against the oracle, at sizes whose
+    # early passes carry their factors in per-q matrices E_q (four CTAs of
+    # a group on neighbouring q; pass 0 and the folded passes before the
+    # last one end in Barrett)
+    plan = matrix_plan(field, log_n)
+    try:
+        desc = N.ntt_plan_describe(plan)
+        assert desc["matrix_folded_passes"] == FOLDED[log_n]
+        x = uniform_elements(field, 1 << log_n, 47000 + log_n)
+        d_x = dev(x)
+        for kind in KINDS:
+            d_y = torch.empty_like(d_x)
+            N.ntt_execute(plan, kind, d_x, d_y)
+            assert np.array_equal(host(d_y), oracle.c_transform(field, kind, x)), (field, log_n, kind)
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
+def test_matrix_folded_custom_shift_in_place():
+    # a new coset shift rebuilds the folded coset matrices; in-place calls
+    # run the folded passes on the plan's scratch
+    field, log_n = "bls12_381_fr", 17
+    f = O.get_field(field)
+    s = 0x1234567890ABCDEF1357 % f.modulus
+    x = uniform_elements(field, 1 << log_n, 47100)
+    plan = matrix_plan(field, log_n)
+    try:
+        assert N.ntt_plan_describe(plan)["matrix_folded_passes"] == 1
+        N.ntt_plan_set_coset_shift(plan, s)
+        for kind in ("coset", "coset_inverse", "forward"):
+            d = dev(x)
+            N.ntt_execute(plan, kind, d, d)
+            assert np.array_equal(host(d), oracle.c_transform(field, kind, x, shift=s)), kind
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("kind", ["forward", "inverse"])
 def test_matrix_equals_butterfly_and_oracle_at_2_20(kind):
     field, log_n = "bls12_381_fr", 20
@@ -140,6 +189,7 @@ def test_matrix_path_bls12_381_2_24_matches_oracle_digest(kind):
     assert hashlib.sha256(x.astype("<u8").tobytes()).hexdigest() == want["input_sha256"]
     plan = matrix_plan(field, log_n, coset=False)
     try:
+        assert N.ntt_plan_describe(plan)["matrix_folded_passes"] == FOLDED[24]
         d_x = dev(x)
         d_y = torch.empty_like(d_x)
         N.ntt_execute(plan, kind, d_x, d_y)
