@@ -41,17 +41,19 @@
 // before needs no factor and ends in Barrett.
 //
 // Kernel structure (persistent, one CTA per SM, warp-specialised):
-//   warp 0       TMA loader: one tensor-map copy (cp.async.bulk.tensor) per
-//                chunk -- the 128 rows of one input n of a tile, whatever
-//                their stride -- into a staging ring; also loads E (E_q of
-//                a folded pass, again whenever q changes, once the MMAs
-//                reading the previous one are complete);
-//   warp 1       MMA issuer: two tcgen05.mma (K = 16 each) per chunk into a
+//   warp 0       MMA issuer: two tcgen05.mma (K = 16 each) per chunk into a
 //                double-buffered TMEM accumulator (N = 32 S columns each);
-//   warps 2-3    digit converters: staging element -> 32 fp16 digits by byte
+//                also loads E by cp.async.bulk (E_q of a folded pass, again
+//                whenever q changes, once the MMAs reading the previous one
+//                are complete);
+//   warps 1-3    converter-loaders: chunk g (the 128 rows of one input n of
+//                a tile, whatever their stride) is loaded by one tensor-map
+//                copy (cp.async.bulk.tensor) into a staging ring and
+//                converted -- staging element -> 32 fp16 digits by byte
 //                permutes (0x64 | byte = 1024 + byte as fp16) and one packed
-//                fp16 subtraction, written as the A operand chunk (the two
-//                warps take alternate chunks, four rows per thread);
+//                fp16 subtraction -- into the A operand ring, both by warp
+//                g mod 3 (four rows per thread), which issues the copy of
+//                chunk g + 18 into the slot once its lanes have read it;
 //   warps 4-19   epilogue: tcgen05.ld of one output's 32 accumulators (and
 //                tcgen05.st of the bias back into them for the buffer's next
 //                tile), ByteMerge by funnel shifts and carry chains, the
@@ -72,17 +74,21 @@
 namespace gb300ntt {
 
 constexpr int kMatRows = 128;                 // sub-transforms per tile (MMA M)
-constexpr int kMatConvWarps = 2;              // alternate chunks; four tile rows per thread
+// Converter warps (1-3, one on each of three SM sub-partitions; the MMA
+// warp is on the fourth): chunk g goes to converter g mod 3, which also
+// loads it, so every ring slot always belongs to the same converter.
+constexpr int kMatConvWarps = 3;
 constexpr int kMatEpiWarps = 16;              // four per TMEM lane quarter
-constexpr int kMatFirstEpiWarp = 2 + kMatConvWarps;
+constexpr int kMatFirstEpiWarp = 1 + kMatConvWarps;
 // 20 warps: five per SM sub-partition, so up to 102 registers per thread
 // fit its 16K-entry register file (22 warps would cap them at 80)
 constexpr int kMatThreads = 32 * (kMatFirstEpiWarp + kMatEpiWarps);   // 640
 // Chunks in flight: the staging ring must cover the latency of the input
-// loads from HBM (16 x 4 KiB = two tiles ahead); the A-operand ring only the
-// hand-off from the converters to the MMA issuer within the SM.
-constexpr int kMatStageRing = 16;
-constexpr int kMatRing = 4;
+// loads from HBM (18 x 4 KiB, over two tiles ahead); the A-operand ring only
+// the hand-off from the converters to the MMA issuer within the SM.  Both
+// are multiples of the converter count.
+constexpr int kMatStageRing = 18;
+constexpr int kMatRing = 3;
 constexpr uint32_t kMatChunkBytes = kMatRows * 32 * 2;   // A chunk: 128 rows x 32 fp16 digits
 constexpr uint32_t kMatStageBytes = kMatRows * 32;       // staging: 128 elements
 constexpr uint32_t kMatFp32Magic = 0x4B400000u;          // bits of 1.5 * 2^23
@@ -388,6 +394,7 @@ __global__ void __launch_bounds__(kMatThreads, 1)
   static_assert(NC <= 256 && NC % 16 == 0, "one MMA covers all outputs");
   static_assert(matrix_smem_bytes<LOGS>() <= 227 * 1024 - 1024, "shared memory");
   static_assert(kMatRing % kMatConvWarps == 0 && kMatStageRing % kMatConvWarps == 0, "slots of one converter");
+  static_assert(kMatFirstEpiWarp == 4, "epilogue warps start on sub-partition 0");
   extern __shared__ __align__(1024) uint8_t mat_smem[];
   uint8_t *sE = mat_smem;
   uint8_t *sA = mat_smem + E_BYTES;
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(kMatThreads, 1)
     mbar_init(&bar_e, 1);
     for (int i = 0; i < kMatStageRing; ++i) {
       mbar_init(&stage_full[i], 1);
-      mbar_init(&stage_empty[i], 32);   // the converter warp of the chunk
+      mbar_init(&stage_empty[i], 32);   // the lanes of the slot's converter warp
     }
     for (int i = 0; i < kMatRing; ++i) {
       mbar_init(&chunk_full[i], 32);
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(kMatThreads, 1)
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_taddr)),
                  "n"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -454,8 +461,9 @@ __global__ void __launch_bounds__(kMatThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = s_taddr;
 
-  uint64_t loads_issued = 0;   // (loader thread) stage uses, for the teardown
-  uint64_t e_issued = 0;       // (loader thread) E loads, for the teardown
+  uint64_t e_issued = 0;       // (MMA thread) E loads, for the teardown
+  uint64_t loads_issued = 0;   // (converter lane 0) last chunk it loaded + 1, for the teardown
+  const uint32_t cw = warp - 1;   // converter index (warps 1 .. kMatConvWarps)
   // E (of a folded pass: E_q) into shared memory, completing on bar_e
   auto load_e = [&](uint64_t q) {
     const uint8_t *src = reinterpret_cast<const uint8_t *>(ma.e) + q * (uint64_t)E_BYTES;
@@ -465,6 +473,18 @@ __global__ void __launch_bounds__(kMatThreads, 1)
       bulk_g2s(sE + off, src + off, bytes, &bar_e);
     }
   };
+  // Chunk g (input g mod S of tile g / S) into staging slot g mod
+  // kMatStageRing: one tensor-map copy of the tile's 128 rows of that input,
+  // whatever their stride in memory.
+  const uint32_t chunk_bytes = (uint32_t)(a.num_sub < (uint64_t)kMatRows ? a.num_sub : kMatRows) * 32u;
+  auto load_chunk = [&](uint64_t g) {
+    const uint32_t sl = (uint32_t)(g % kMatStageRing);
+    const uint64_t d0 = tile_d0(u_begin + g / S);
+    mbar_expect_tx(&stage_full[sl], chunk_bytes);
+    tma_load_4d(sStage + sl * kMatStageBytes, &in_map, 0, (int)(d0 & mp_mask), (int)(g % S), (int)(d0 >> a.log_mp),
+                &stage_full[sl]);
+  };
+  const uint64_t chunks = my_tiles * S;
   // E and the factor tables are plan constants: the first E is requested
   // before the wait for the previous launch (programmatic dependent launch),
   // every access to the vector comes after it.
@@ -476,40 +496,9 @@ __global__ void __launch_bounds__(kMatThreads, 1)
   pdl_trigger_and_wait();
 
   if (warp == 0) {
-    // ------------------------------------------------------ TMA loader
-    // Lane 0: one tensor-map copy per chunk (the 128 rows of input n of the
-    // tile, whatever their stride in memory) into the staging ring; for a
-    // folded pass, E_q again whenever q changes, once the MMAs that read the
-    // previous E are done.
-    if (lane == 0) {
-      const uint32_t chunk_bytes = (uint32_t)(a.num_sub < (uint64_t)kMatRows ? a.num_sub : kMatRows) * 32u;
-      uint64_t g = 0;
-      bool ok = true;
-      for (uint64_t it = 0; ok && it < my_tiles && !*abort; ++it) {
-        const uint64_t t = u_begin + it;
-        if (it > 0 && ma.fold && tile_q(t) != tile_q(t - 1)) {
-          ok = mbar_wait(&bar_efree, (uint32_t)((e_issued - 1) & 1), ma, abort);
-          if (!ok) break;
-          load_e(tile_q(t));
-          ++e_issued;
-        }
-        const uint64_t d0 = tile_d0(t);
-        const int c1 = (int)(d0 & mp_mask), c3 = (int)(d0 >> a.log_mp);
-        for (uint32_t n = 0; n < S; ++n, ++g) {
-          const uint32_t s = (uint32_t)(g % kMatStageRing);
-          const uint64_t u = g / kMatStageRing;
-          if (u >= 1 && !mbar_wait(&stage_empty[s], (uint32_t)((u - 1) & 1), ma, abort)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&stage_full[s], chunk_bytes);
-          tma_load_4d(sStage + s * kMatStageBytes, &in_map, 0, c1, (int)n, c3, &stage_full[s]);
-          loads_issued = g + 1;
-        }
-      }
-    }
-  } else if (warp == 1) {
     // ------------------------------------------------------ MMA issuer
+    // Lane 0; for a folded pass also E_q again whenever q changes, once the
+    // MMAs reading the previous E are complete.
     if (lane == 0) {
       // fp32 accumulate (bit 4), fp16 A and B (formats 0), K-major both,
       // N >> 3 at bit 17, M >> 4 at bit 24
@@ -520,7 +509,13 @@ __global__ void __launch_bounds__(kMatThreads, 1)
       uint64_t g = 0;
       for (uint64_t it = 0; ok && it < my_tiles; ++it) {
         const uint64_t t = u_begin + it;
-        if (it == 0 || (ma.fold && tile_q(t) != tile_q(t - 1))) {
+        const bool new_e = it == 0 || (ma.fold && tile_q(t) != tile_q(t - 1));
+        if (it > 0 && new_e) {
+          if (!mbar_wait(&bar_efree, (uint32_t)((e_issued - 1) & 1), ma, abort)) break;
+          load_e(tile_q(t));
+          ++e_issued;
+        }
+        if (new_e) {
           if (!mbar_wait(&bar_e, (uint32_t)(e_used & 1), ma, abort)) break;
           ++e_used;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -564,12 +559,16 @@ __global__ void __launch_bounds__(kMatThreads, 1)
       }
     }
   } else if (warp < kMatFirstEpiWarp) {
-    // ------------------------------------------------------ digit converters
-    // Converter warp cw takes the chunks g = cw, cw + 2, ... (ring slots of
-    // one parity: both ring sizes are even), each thread the rows lane,
-    // lane + 32, lane + 64, lane + 96.
-    const uint32_t cw = warp - 2;
-    const uint64_t chunks = my_tiles * S;
+    // ------------------------------------------------------ converter-loaders
+    // Converter cw takes the chunks g = cw, cw + 3, ... (staging and operand
+    // slots g mod 18 and g mod 3: always its own), each thread the rows
+    // lane, lane + 32, lane + 64, lane + 96; lane 0 loads the converter's
+    // chunks, the next one into a slot as soon as the warp has read it.
+    if (lane == 0)
+      for (uint64_t g = cw; g < chunks && g < (uint64_t)kMatStageRing; g += kMatConvWarps) {
+        load_chunk(g);
+        loads_issued = g + 1;
+      }
     for (uint64_t g = cw; g < chunks && !*abort; g += kMatConvWarps) {
       const uint32_t sl = (uint32_t)(g % kMatStageRing);
       const uint64_t us = g / kMatStageRing;
@@ -591,9 +590,16 @@ __global__ void __launch_bounds__(kMatThreads, 1)
           *reinterpret_cast<uint4 *>(dst + core_offset(m, 8 * q, 32)) =
               make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
       }
+      // the operand writes before the MMA reads them (async proxy); every
+      // lane's staging reads before lane 0 copies the next chunk into the slot
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&stage_empty[sl]);
       mbar_arrive(&chunk_full[c]);
+      if (lane == 0 && g + kMatStageRing < chunks) {
+        if (!mbar_wait(&stage_empty[sl], (uint32_t)(us & 1), ma, abort)) break;
+        load_chunk(g + kMatStageRing);
+        loads_issued = g + kMatStageRing + 1;
+      }
     }
   } else {
     // ------------------------------------------------------ epilogue
@@ -697,29 +703,29 @@ __global__ void __launch_bounds__(kMatThreads, 1)
   // shared memory and TMEM go away.  Normally these waits return at once;
   // after an abort they are bounded like every other wait.
   __syncthreads();
+  if (warp >= 1 && warp < kMatFirstEpiWarp && lane == 0) {
+    // the last copy into each of this converter's staging slots
+    const uint64_t t0 = mat_global_ns();
+    for (uint64_t sl = cw; sl < (uint64_t)kMatStageRing && sl < loads_issued; sl += kMatConvWarps) {
+      const uint64_t g = sl + ((loads_issued - 1 - sl) / kMatStageRing) * kMatStageRing;
+      while (!mbar_try(&stage_full[sl], (uint32_t)((g / kMatStageRing) & 1)) && mat_global_ns() - t0 < ma.wait_ns) {
+      }
+    }
+  }
   if (tid == 0) {
     const uint64_t t0 = mat_global_ns();
     while (e_issued && !mbar_try(&bar_e, (uint32_t)((e_issued - 1) & 1)) && mat_global_ns() - t0 < ma.wait_ns) {
     }
-    // last use u of each staging slot s: completion #u has parity u & 1
-    for (uint64_t s = 0; s < (uint64_t)kMatStageRing && s < loads_issued; ++s) {
-      const uint64_t u = (loads_issued - 1 - s) / kMatStageRing;
-      while (!mbar_try(&stage_full[s], (uint32_t)(u & 1)) && mat_global_ns() - t0 < ma.wait_ns) {
-      }
-    }
-  }
-  if (tid == 32) {
     // a commit tracks every MMA this thread issued before it
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_addr(&bar_done))
                  : "memory");
-    const uint64_t t0 = mat_global_ns();
     while (!mbar_try(&bar_done, 0) && mat_global_ns() - t0 < ma.wait_ns) {
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(TMEM_COLS));
   }
