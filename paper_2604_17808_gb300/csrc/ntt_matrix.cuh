@@ -53,7 +53,7 @@
 //                permutes (0x64 | byte = 1024 + byte as fp16) and one packed
 //                fp16 subtraction -- into the A operand ring, both by warp
 //                g mod 3 (four rows per thread), which issues the copy of
-//                chunk g + 18 into the slot once its lanes have read it;
+//                chunk g + 12 into the slot once its lanes have read it;
 //   warps 4-19   epilogue: tcgen05.ld of one output's 32 accumulators (and
 //                tcgen05.st of the bias back into them for the buffer's next
 //                tile), ByteMerge by funnel shifts and carry chains, the
@@ -83,12 +83,13 @@ constexpr int kMatFirstEpiWarp = 1 + kMatConvWarps;
 // 20 warps: five per SM sub-partition, so up to 102 registers per thread
 // fit its 16K-entry register file (22 warps would cap them at 80)
 constexpr int kMatThreads = 32 * (kMatFirstEpiWarp + kMatEpiWarps);   // 640
-// Chunks in flight: the staging ring must cover the latency of the input
-// loads from HBM (18 x 4 KiB, over two tiles ahead); the A-operand ring only
-// the hand-off from the converters to the MMA issuer within the SM.  Both
+// Chunks in flight: the staging ring covers the latency of the input loads
+// from HBM (12 x 4 KiB, one and a half tiles ahead); the A-operand ring the
+// hand-off from the converters to the MMA issuer, two slots per converter so
+// that it converts its next chunk while the MMAs read the last one.  Both
 // are multiples of the converter count.
-constexpr int kMatStageRing = 18;
-constexpr int kMatRing = 3;
+constexpr int kMatStageRing = 12;
+constexpr int kMatRing = 6;
 constexpr uint32_t kMatChunkBytes = kMatRows * 32 * 2;   // A chunk: 128 rows x 32 fp16 digits
 constexpr uint32_t kMatStageBytes = kMatRows * 32;       // staging: 128 elements
 constexpr uint32_t kMatFp32Magic = 0x4B400000u;          // bits of 1.5 * 2^23
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(kMatThreads, 1)
   } else if (warp < kMatFirstEpiWarp) {
     // ------------------------------------------------------ converter-loaders
     // Converter cw takes the chunks g = cw, cw + 3, ... (staging and operand
-    // slots g mod 18 and g mod 3: always its own), each thread the rows
+    // slots g mod 12 and g mod 6: always its own), each thread the rows
     // lane, lane + 32, lane + 64, lane + 96; lane 0 loads the converter's
     // chunks, the next one into a slot as soon as the warp has read it.
     if (lane == 0)
