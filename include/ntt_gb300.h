@@ -323,7 +323,8 @@ ntt_status ntt_batch_autotune(const ntt_job *jobs, size_t n, uint32_t reps, ntt_
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, which may load the library's device code on that
- * device); make that first call before any stream capture.  The address is
+ * device, and so may allocate): make that first call before the phase in
+ * which the caller must not allocate.  The address is
  * kept until ntt_batch_cache_clear, which must be called after a
  * cudaDeviceReset.  Every call on a device shares the one array, which keeps
  * the last call's contents (the call clears the counters it needs): calls
