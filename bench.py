@@ -327,11 +327,24 @@ def measure_2_24(torch, N, stream, steps: int) -> dict:
         torch.cuda.synchronize()
         same = bool(torch.equal(ym, ys[0]))
         mdesc = N.ntt_plan_describe(plan)
+        # composite bound of the matrix path: per pass the larger of its HBM
+        # time (one read and one write of 32 B per element) and its tensor
+        # time (2 * 32 S * 32 S flops per sub-transform of S points)
+        pk = peaks()
+        hbm = pk.get("hbm_gbs", 6800.0) * 1e9
+        tc = pk.get("bf16_tflops", 1900.0) * 1e12
+        t_min = sum(max((1 << log_n) * 64 / hbm, (1 << log_n) * 2048 * (1 << ls) / tc) for ls in mdesc["pass_log"])
         return {"workload": "BLS12-381 Fr forward NTT, n=2^24, butterfly path", "ms": round(ms, 4),
                 "elements_per_s": (1 << log_n) / (ms * 1e-3),
                 "imad_roofline_frac": round(alg / (ms * 1e-3) / 1e12 / peak, 4), "passes": per_pass,
                 "matrix_path": {"ms": round(ms_m, 4), "elements_per_s": (1 << log_n) / (ms_m * 1e-3),
-                                "passes": mdesc["launches_per_transform"], "identical_to_butterfly": same,
+                                "passes": mdesc["launches_per_transform"],
+                                "folded_passes": mdesc["matrix_folded_passes"], "identical_to_butterfly": same,
+                                "composite_bound_ms": round(t_min * 1e3, 4),
+                                "composite_frac": round(t_min * 1e3 / ms_m, 4),
+                                "bound_note": "sum over passes of max(64 B/element at the measured HBM copy rate, "
+                                              "2048 S flops/element at the measured bf16 (= fp16) tensor rate); "
+                                              "the epilogue's modular reduction (IMAD pipe) is not in it",
                                 "device_error": N.ntt_plan_poll_error(plan)}}
     finally:
         N.ntt_plan_destroy(plan)
