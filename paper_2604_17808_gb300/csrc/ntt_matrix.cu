@@ -140,7 +140,8 @@ void build_e16(const HostField &F, uint32_t logs, const std::vector<U256> &V, bo
   }
 }
 
-ntt_status upload(ntt_plan p, const std::vector<uint8_t> &buf, uint4 **out) {
+template <class T>
+ntt_status upload(ntt_plan, const std::vector<uint8_t> &buf, T **out) {
   if (*out) {
     cudaFree(*out);
     *out = nullptr;
@@ -313,7 +314,7 @@ ntt_status build_fold_tables(ntt_plan p, int tk) {
     s = upload(p, all, &m->e_fold[tk][j]);
     std::vector<uint8_t> ob(offs.size() * sizeof(uint32_t));
     std::memcpy(ob.data(), offs.data(), ob.size());
-    if (s == NTT_OK) s = upload(p, ob, reinterpret_cast<uint4 **>(&m->off_fold[tk][j]));
+    if (s == NTT_OK) s = upload(p, ob, &m->off_fold[tk][j]);
     if (s != NTT_OK) return s;
   }
   return NTT_OK;
