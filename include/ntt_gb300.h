@@ -162,8 +162,9 @@ ntt_status ntt_transform_host_async(ntt_plan plan, ntt_kind kind, const void *h_
                                     ntt_stream stream);
 
 /*
- * Read back the plan's structure: number of passes, the log2 size of each
- * pass's sub-transforms (up to 4), the number of kernel launches one
+ * Read back the plan's structure: number of passes and the log2 size of each
+ * pass's sub-transforms (of the path selected: on the matrix path its own
+ * split into passes of at most 2^3 points), the number of kernel launches one
  * transform makes and, on the matrix path, how many of its passes
  * (passes 1 .. matrix_folded_passes) take their input factors folded into
  * per-q byte matrices (so that the pass before them ends in a Barrett

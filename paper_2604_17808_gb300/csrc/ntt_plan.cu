@@ -483,8 +483,10 @@ ntt_status ntt_plan_describe(ntt_plan plan, ntt_plan_desc *out) {
   std::memset(out, 0, sizeof *out);
   out->field = (uint32_t)plan->field;
   out->log_n = plan->log_n;
-  out->num_passes = plan->num_passes;
-  for (uint32_t j = 0; j < plan->num_passes && j < NTT_MAX_PASSES; ++j) out->pass_log[j] = plan->pass_log[j];
+  // the passes of the path that runs: the matrix path's own split when it is selected
+  const ntt_plan run = plan->path == NTT_PATH_MATRIX && plan->matrix && plan->matrix->nested ? plan->matrix->nested : plan;
+  out->num_passes = run->num_passes;
+  for (uint32_t j = 0; j < run->num_passes && j < NTT_MAX_PASSES; ++j) out->pass_log[j] = run->pass_log[j];
   out->launches_per_transform = plan->path == NTT_PATH_MATRIX ? matrix_launches(plan) : plan->launches;
   out->path = (uint32_t)plan->path;
   out->device_bytes = plan->device_bytes;

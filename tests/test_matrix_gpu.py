@@ -55,6 +55,9 @@ def test_matrix_path_all_small_sizes_and_kinds(field):
         try:
             desc = N.ntt_plan_describe(plan)
             assert desc["path"] == 2 and desc["launches_per_transform"] == -(-log_n // 3)
+            # the described split is the matrix path's own: passes of <= 2^3 points
+            assert len(desc["pass_log"]) == desc["num_passes"] == -(-log_n // 3)
+            assert sum(desc["pass_log"]) == log_n and max(desc["pass_log"]) <= 3
             for kind in KINDS:
                 x = uniform_elements(field, 1 << log_n, 40000 + log_n)
                 d_x = dev(x)
