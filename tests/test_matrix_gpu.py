@@ -118,6 +118,30 @@ def test_matrix_folded_passes_all_kinds(field, log_n):
         N.ntt_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("field", FIELDS)
+@pytest.mark.parametrize("log_n", [21, 22])
+def test_matrix_folded_coset_kinds_larger(field, log_n):
+    # passes of 2^3 and (2^22) 2^2 points, two folded; the coset forward
+    # (coset powers in the pass-0 matrix, coset inverse's s^-n in the last
+    # epilogue) element by element against the oracle (its all-cores mode,
+    # which the CPU tests pin to the serial loop)
+    plan = matrix_plan(field, log_n)
+    threads = oracle.c_set_threads(0)
+    try:
+        desc = N.ntt_plan_describe(plan)
+        assert desc["matrix_folded_passes"] == 2 and sum(desc["pass_log"]) == log_n
+        x = uniform_elements(field, 1 << log_n, 47200 + log_n)
+        d_x = dev(x)
+        for kind in ("coset", "coset_inverse"):
+            d_y = torch.empty_like(d_x)
+            N.ntt_execute(plan, kind, d_x, d_y)
+            assert np.array_equal(host(d_y), oracle.c_transform(field, kind, x)), (field, log_n, kind, threads)
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        oracle.c_set_threads(1)
+        N.ntt_plan_destroy(plan)
+
+
 def test_matrix_folded_custom_shift_in_place():
     # a new coset shift rebuilds the folded coset matrices; in-place calls
     # run the folded passes on the plan's scratch
