@@ -142,6 +142,29 @@ def test_matrix_folded_coset_kinds_larger(field, log_n):
         N.ntt_plan_destroy(plan)
 
 
+def test_matrix_path_2_26_four_folded_passes():
+    # 2^26 (2 GiB per vector): passes 1-4 folded (pass 4 with 4096 matrices
+    # E_q); the forward output equals the butterfly path's byte for byte and
+    # the inverse gives the input back
+    field, log_n = "bls12_381_fr", 26
+    plan = N.ntt_plan_create(field, log_n, coset=False)
+    try:
+        x = torch.from_numpy(np.tile(uniform_elements(field, 1 << 20, 47300), (1 << 6, 1)).view(np.int64)).cuda()
+        yb = torch.empty_like(x)
+        N.ntt_execute(plan, "forward", x, yb)
+        N.ntt_plan_set_path(plan, "matrix")
+        assert N.ntt_plan_describe(plan)["matrix_folded_passes"] == 4
+        ym = torch.empty_like(x)
+        N.ntt_execute(plan, "forward", x, ym)
+        assert torch.equal(ym, yb)
+        del yb
+        N.ntt_execute(plan, "inverse", ym, ym)
+        assert torch.equal(ym, x)
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+
+
 def test_matrix_folded_custom_shift_in_place():
     # a new coset shift rebuilds the folded coset matrices; in-place calls
     # run the folded passes on the plan's scratch
