@@ -114,7 +114,16 @@ typedef struct ntt_plan_s *ntt_plan;
  */
 ntt_status ntt_plan_create(ntt_plan *out, ntt_field field, uint32_t log_n, int coset);
 
-/* Choose the path used by later transforms on this plan. */
+/*
+ * Choose the path used by later transforms on this plan.  The first switch
+ * to NTT_PATH_MATRIX builds that path's resources: a nested plan of passes of
+ * at most 2^3 points with its own tables, the byte matrices E of its passes
+ * and, from 2^17 points on, the per-q matrices of its folded passes (built on
+ * the host's cores; at 2^24 about 73 MB per table kind and well under a
+ * second; more than 1 GB from 2^26 on).  They stay with the plan until it is
+ * destroyed; switching back and forth costs nothing more.  Outputs are
+ * byte-identical on both paths.
+ */
 ntt_status ntt_plan_set_path(ntt_plan plan, ntt_path path);
 
 /*
