@@ -39,7 +39,7 @@ def main() -> None:
         # (configuration index, field, log_n, kinds, seed)
         (1, "bls12_381_fr", 12, ["forward", "inverse"], config_seed(1)),
         (2, "bls12_381_fr", 20, ["forward", "inverse"], config_seed(2)),
-        (3, "bn254_fr", 24, ["coset"], config_seed(3)),
+        (3, "bn254_fr", 24, ["coset", "coset_inverse"], config_seed(3)),
         # the 2^24-point BLS12-381 transform (the size the 2^24 measurements use)
         (3, "bls12_381_fr", 24, ["forward", "inverse"], config_seed(3, 100)),
     ]

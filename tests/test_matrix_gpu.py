@@ -227,6 +227,30 @@ def test_matrix_path_bn254_2_24_coset_matches_oracle_digest():
     assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == want["output_sha256"]
 
 
+@pytest.mark.parametrize("path", ["butterfly", "matrix"])
+def test_bn254_2_24_coset_inverse_matches_oracle_digest(path):
+    # the coset inverse of the BN254 2^24 workload vector (s^-n applied to the
+    # last pass's outputs; on the matrix path by the last epilogue's
+    # Montgomery product), whole output against the stored oracle digest
+    field, log_n = "bn254_fr", 24
+    x = uniform_elements(field, 1 << log_n, config_seed(3))
+    with open(os.path.join(HERE, "golden", "oracle_digests.json")) as fh:
+        want = [c for c in json.load(fh)["single"]
+                if c["config"] == 3 and c["kind"] == "coset_inverse" and c["field"] == field][0]
+    assert hashlib.sha256(x.astype("<u8").tobytes()).hexdigest() == want["input_sha256"]
+    plan = N.ntt_plan_create(field, log_n)
+    try:
+        N.ntt_plan_set_path(plan, path)
+        d_x = dev(x)
+        d_y = torch.empty_like(d_x)
+        N.ntt_execute(plan, "coset_inverse", d_x, d_y)
+        got = host(d_y)
+        assert N.ntt_plan_poll_error(plan) == 0
+    finally:
+        N.ntt_plan_destroy(plan)
+    assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == want["output_sha256"]
+
+
 @pytest.mark.parametrize("kind", ["forward", "inverse"])
 def test_matrix_path_bls12_381_2_24_matches_oracle_digest(kind):
     # the 2^24-point BLS12-381 transform on the tensor-core path, whole output
