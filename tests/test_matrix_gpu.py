@@ -238,7 +238,7 @@ def test_bn254_2_24_coset_inverse_matches_oracle_digest(path):
         want = [c for c in json.load(fh)["single"]
                 if c["config"] == 3 and c["kind"] == "coset_inverse" and c["field"] == field][0]
     assert hashlib.sha256(x.astype("<u8").tobytes()).hexdigest() == want["input_sha256"]
-    plan = N.ntt_plan_create(field, log_n)
+    plan = N.ntt_plan_create(field, log_n, coset=True)
     try:
         N.ntt_plan_set_path(plan, path)
         d_x = dev(x)
