@@ -497,6 +497,7 @@ ntt_status enqueue_matrix_transform(ntt_plan p, int kind, const void *in, void *
       std::memcpy(ma.off, m->off_inner[dir][logs][sc], sizeof ma.off);
     }
     ma.barrett = barrett ? 1u : 0u;
+    ma.lazy = j + 1 < P ? 1u : 0u;   // the last pass's outputs are canonical
     ma.mu = m->mu;
     if (!ma.e) return NTT_ERR_UNSUPPORTED;
     if (j + 1 < P && !barrett) {

@@ -32,8 +32,11 @@
 // [2^23, 2^24], exact in fp32, and the final fp32 bit pattern is 0x4B400000
 // + acc: the accumulators are read as integers with no conversion at all.
 // Z < 2^31 2^248 (256/255) + p < 2^280, so the 9-row Montgomery product (R =
-// 2^288) of Z and T < p ends below 2p and one conditional subtraction makes
-// it canonical; the last pass (no factor) uses a Barrett reduction instead.
+// 2^288) of Z and T < p ends below 2p; the last pass (no factor) uses a
+// Barrett reduction instead, which also ends below 2p.  Only the last pass
+// subtracts p once more to make its outputs canonical: a value in [0, 2p) is
+// below 2^256, and a pass takes the bytes of any 256-bit input (its digits,
+// offsets and bounds do not assume x < p).
 //
 // Folded passes (early passes: few q, many rows each): the rows d = q + o Mp
 // of a tile share q, and the pass's own input factors c(q, n) are folded
@@ -115,6 +118,7 @@ struct MatrixPassArgs {
   uint32_t fold_group;
   uint32_t tiles_per_q_log;   // log2 of the 128-row blocks of o per q
   const uint32_t *off_fold;
+  uint32_t lazy;          // 1: outputs left in [0, 2p) (every pass but the last)
   uint32_t *err;          // device error word
   uint64_t wait_ns;       // bound of every wait
 };
@@ -310,9 +314,10 @@ __device__ __forceinline__ void byte_merge(uint32_t z[9], const uint32_t u[32], 
 // r = z * t * 2^-288 mod p for z < 2^280 (nine limbs) and canonical t: the
 // CIOS rows of mont_mul (fp256.cuh) over the nine limbs of z.  The running
 // value stays below 2^288 (as in mont_mul: t < p, one limb of z per row) and
-// the result is below 2p, so one conditional subtraction makes it canonical.
+// the result is below 2p; one conditional subtraction makes it canonical
+// (lazy: left in [0, 2p) for a pass that is not the last).
 template <class F>
-__device__ __forceinline__ void mont_mul_z9(uint32_t r[8], const uint32_t z[9], const uint32_t t[8]) {
+__device__ __forceinline__ void mont_mul_z9(uint32_t r[8], const uint32_t z[9], const uint32_t t[8], bool lazy) {
   uint32_t acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -325,15 +330,21 @@ __device__ __forceinline__ void mont_mul_z9(uint32_t r[8], const uint32_t z[9], 
     for (int j = 0; j < 8; ++j) acc[j] = acc[j + 1];
     acc[8] = 0;
   }
-  reduce_once<F>(r, acc);
+  if (lazy) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = acc[j];   // in [0, 2p): the next pass takes any 256-bit input
+  } else {
+    reduce_once<F>(r, acc);
+  }
 }
 
-// r = z mod p, canonical, for z < 2^280 (nine limbs): q = floor(floor(z /
-// 2^224) mu / 2^64) with mu = floor(2^288 / p) is floor(z / p) or one less
-// (the truncations lose less than 2^-30 + 2^-8), so z - q p lies in [0, 2p)
-// and one conditional subtraction finishes.  q < 2^27.
+// r = z mod p for z < 2^280 (nine limbs): q = floor(floor(z / 2^224) mu /
+// 2^64) with mu = floor(2^288 / p) is floor(z / p) or one less (the
+// truncations lose less than 2^-30 + 2^-8), so z - q p lies in [0, 2p) and
+// one conditional subtraction makes it canonical (lazy: left in [0, 2p)).
+// q < 2^27.
 template <class F>
-__device__ __forceinline__ void barrett_z9(uint32_t r[8], const uint32_t z[9], uint64_t mu) {
+__device__ __forceinline__ void barrett_z9(uint32_t r[8], const uint32_t z[9], uint64_t mu, bool lazy) {
   const uint64_t zt = ((uint64_t)z[8] << 32) | z[7];
   const uint32_t q = (uint32_t)__umul64hi(zt, mu);
   uint32_t qp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -351,7 +362,12 @@ __device__ __forceinline__ void barrett_z9(uint32_t r[8], const uint32_t z[9], u
       : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7])
       : "r"(z[0]), "r"(z[1]), "r"(z[2]), "r"(z[3]), "r"(z[4]), "r"(z[5]), "r"(z[6]), "r"(z[7]), "r"(qp[0]),
         "r"(qp[1]), "r"(qp[2]), "r"(qp[3]), "r"(qp[4]), "r"(qp[5]), "r"(qp[6]), "r"(qp[7]));
-  reduce_once<F>(r, d);
+  if (lazy) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = d[j];
+  } else {
+    reduce_once<F>(r, d);
+  }
 }
 
 // Position of input n (or, for inner passes, output n) of sub-transform d.
@@ -409,6 +425,7 @@ __global__ void __launch_bounds__(kMatThreads, 1)
   __shared__ int s_abort;
   volatile int *abort = &s_abort;
   const PassArgs &a = ma.a;
+  const bool lazy = ma.lazy != 0;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // Work units: tiles (128 consecutive rows d) of the plain pass; for a
   // folded pass (q group, o block) pairs of the CTA's group.  Each CTA takes
@@ -680,15 +697,15 @@ __global__ void __launch_bounds__(kMatThreads, 1)
         uint32_t y[2][8];
         if (kOuts == 2) {
           if (ma.barrett) {
-            barrett_z9<F>(y[0], z[0], ma.mu);
-            barrett_z9<F>(y[1], z[1], ma.mu);
+            barrett_z9<F>(y[0], z[0], ma.mu, lazy);
+            barrett_z9<F>(y[1], z[1], ma.mu, lazy);
           } else {
-            mont_mul_z9<F>(y[0], z[0], fac[0]);
-            mont_mul_z9<F>(y[1], z[1], fac[1]);
+            mont_mul_z9<F>(y[0], z[0], fac[0], lazy);
+            mont_mul_z9<F>(y[1], z[1], fac[1], lazy);
           }
         } else {
-          if (ma.barrett) barrett_z9<F>(y[0], z[0], ma.mu);
-          else mont_mul_z9<F>(y[0], z[0], fac[0]);
+          if (ma.barrett) barrett_z9<F>(y[0], z[0], ma.mu, lazy);
+          else mont_mul_z9<F>(y[0], z[0], fac[0], lazy);
         }
 #pragma unroll
         for (int o = 0; o < kOuts; ++o) fe_store_global(a.dst, pos[o], y[o]);
