@@ -663,52 +663,43 @@ __global__ void __launch_bounds__(kMatThreads, 1)
       }
       if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // ByteMerge of each output (accumulators back to the bias as they are
-      // read), then the outputs' reductions side by side
-      uint32_t z[2][9];
+      // each output in turn: its accumulators (back to the bias as they are
+      // read), ByteMerge, reduction, store
       constexpr int kOuts = S > 4 ? 2 : 1;
 #pragma unroll
       for (int o = 0; o < kOuts; ++o) {
         const uint32_t k = part + 4 * o;
         if (k >= S) break;
-        uint32_t r[32];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(lane_addr + buf * NC + 32 * k));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        tmem_store_bias(lane_addr + buf * NC + 32 * k);   // for this buffer's next tile
-        if (ma.fold && ma.barrett) {
-          byte_merge(z[o], r, fac[o]);
-        } else if (ma.fold) {
-          uint32_t off[8];
-          fe_load_global(off, offq, k);
-          byte_merge(z[o], r, off);
-        } else {
-          byte_merge(z[o], r, ma.off[k]);
-        }
-      }
-      if (live && part < S) {
-        uint32_t y[2][8];
-        if (kOuts == 2) {
-          if (ma.barrett) {
-            barrett_z9<F>(y[0], z[0], ma.mu, lazy);
-            barrett_z9<F>(y[1], z[1], ma.mu, lazy);
+        uint32_t z[9];
+        {
+          uint32_t r[32];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(lane_addr + buf * NC + 32 * k));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          tmem_store_bias(lane_addr + buf * NC + 32 * k);   // for this buffer's next tile
+          if (ma.fold && ma.barrett) {
+            byte_merge(z, r, fac[o]);
+          } else if (ma.fold) {
+            uint32_t off[8];
+            fe_load_global(off, offq, k);
+            byte_merge(z, r, off);
           } else {
-            mont_mul_z9<F>(y[0], z[0], fac[0], lazy);
-            mont_mul_z9<F>(y[1], z[1], fac[1], lazy);
+            byte_merge(z, r, ma.off[k]);
           }
-        } else {
-          if (ma.barrett) barrett_z9<F>(y[0], z[0], ma.mu, lazy);
-          else mont_mul_z9<F>(y[0], z[0], fac[0], lazy);
         }
-#pragma unroll
-        for (int o = 0; o < kOuts; ++o) fe_store_global(a.dst, pos[o], y[o]);
+        if (live) {
+          uint32_t y[8];
+          if (ma.barrett) barrett_z9<F>(y, z, ma.mu, lazy);
+          else mont_mul_z9<F>(y, z, fac[o], lazy);
+          fe_store_global(a.dst, pos[o], y);
+        }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
