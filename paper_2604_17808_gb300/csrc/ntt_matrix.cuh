@@ -636,29 +636,41 @@ __global__ void __launch_bounds__(kMatThreads, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     mbar_arrive(&acc_empty[0]);
     mbar_arrive(&acc_empty[1]);
+    // factors of this thread's outputs; a folded pass ending in Barrett
+    // needs none and keeps its merge offsets here instead, loaded again only
+    // when q changes
+    uint32_t fac[2][8];
+    uint64_t fac_q = ~0ull;
+    if (!ma.post && !ma.next && !ma.fold) {
+#pragma unroll
+      for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) fac[o][j] = ma.one[j];
+    }
     for (uint64_t it = 0; it < my_tiles; ++it) {
       const uint32_t buf = (uint32_t)(it & 1);
       const uint64_t u = u_begin + it;
       const uint64_t d = tile_d0(u) + m * row_step;
       const bool live = ma.fold || d < a.num_sub;
-      // this thread's outputs k = part and part + 4: positions and factors
-      // are loaded before the accumulators are ready; a folded pass ending
-      // in Barrett needs no factor and preloads its merge offsets instead
+      // positions and factors of the outputs k = part and part + 4 are
+      // loaded before the accumulators are ready
       uint64_t pos[2] = {0, 0};
-      uint32_t fac[2][8];
-      const uint4 *offq = reinterpret_cast<const uint4 *>(ma.off_fold + tile_q(u) * S * 8);   // S entries of q
+      const uint64_t q = tile_q(u);
+      const uint4 *offq = reinterpret_cast<const uint4 *>(ma.off_fold + q * S * 8);   // S entries of q
+      const bool new_off = ma.fold && ma.barrett && q != fac_q;
+      fac_q = q;
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         const uint32_t k = part + 4 * o;
         if (k < S && live) {
           pos[o] = mat_out_pos<LOGS, MODE>(a, d, k);
-          if (ma.fold && ma.barrett) fe_load_global(fac[o], offq, k);
-          else if (ma.post) fe_load_global(fac[o], ma.post, pos[o]);
-          else if (ma.next) fe_load_global(fac[o], ma.next, pos[o] & next_mask);
-        }
-        if (!ma.post && !ma.next && !ma.fold) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) fac[o][j] = ma.one[j];
+          if (ma.fold && ma.barrett) {
+            if (new_off) fe_load_global(fac[o], offq, k);
+          } else if (ma.post) {
+            fe_load_global(fac[o], ma.post, pos[o]);
+          } else if (ma.next) {
+            fe_load_global(fac[o], ma.next, pos[o] & next_mask);
+          }
         }
       }
       if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
