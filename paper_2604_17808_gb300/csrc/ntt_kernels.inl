@@ -281,28 +281,35 @@ cudaError_t prepare_batch() {
 
 namespace {
 
-template <int LOGS, int MODE>
+template <int LOGS, int MODE, bool BARRETT>
 cudaError_t set_matrix_attr() {
-  return cudaFuncSetAttribute(ntt_matrix_pass_kernel<F, LOGS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              matrix_smem_bytes<LOGS>());
+  return cudaFuncSetAttribute(ntt_matrix_pass_kernel<F, LOGS, MODE, BARRETT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, matrix_smem_bytes<LOGS>());
 }
 
 template <int LOGS>
 cudaError_t set_matrix_attrs() {
-  cudaError_t e = set_matrix_attr<LOGS, kModeInner>();
-  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirst>();
+  cudaError_t e = set_matrix_attr<LOGS, kModeInner, false>();
+  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeInner, true>();
+  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirst, false>();
+  if (e == cudaSuccess) e = set_matrix_attr<LOGS, kModeFirst, true>();
   return e;
+}
+
+template <int LOGS, int MODE>
+cudaError_t matrix_mode(const MatrixPassArgs &ma, const CUtensorMap &in_map, uint32_t grid, cudaStream_t st) {
+  const int smem = matrix_smem_bytes<LOGS>();
+  if (ma.barrett)
+    return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, MODE, true>, grid, kMatThreads, smem, st, ma, in_map);
+  return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, MODE, false>, grid, kMatThreads, smem, st, ma, in_map);
 }
 
 template <int LOGS>
 cudaError_t matrix_logs(int mode, const MatrixPassArgs &ma, const CUtensorMap &in_map, uint32_t grid,
                         cudaStream_t st) {
-  const int smem = matrix_smem_bytes<LOGS>();
   switch (mode) {
-    case kModeInner:
-      return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeInner>, grid, kMatThreads, smem, st, ma, in_map);
-    case kModeFirst:
-      return launch_pdl(ntt_matrix_pass_kernel<F, LOGS, kModeFirst>, grid, kMatThreads, smem, st, ma, in_map);
+    case kModeInner: return matrix_mode<LOGS, kModeInner>(ma, in_map, grid, st);
+    case kModeFirst: return matrix_mode<LOGS, kModeFirst>(ma, in_map, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -238,6 +238,19 @@ __device__ __forceinline__ void digits_f16(uint32_t w[16], const uint32_t x[8]) 
   }
 }
 
+// 32 consecutive TMEM columns of this warp's 32 lanes into r (completes at
+// the next tcgen05.wait::ld).
+__device__ __forceinline__ void tmem_ld32(uint32_t r[32], uint32_t taddr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
 // Write the bias 1.5 * 2^23 (fp32 bits 0x4B400000) into 32 consecutive TMEM
 // columns of this warp's 32 lanes: accumulating on top of it, every MMA
 // result is already the pattern 0x4B400000 + acc (see the header).
@@ -399,8 +412,10 @@ __host__ __device__ constexpr int matrix_smem_bytes() {
 }
 
 // One matrix pass (MODE: kModeInner or kModeFirst; pass-0 multipliers are
-// folded into E).
-template <class F, int LOGS, int MODE>
+// folded into E).  BARRETT: the pass ends in the Barrett reduction (no
+// factor); its epilogue issues the second output's accumulator load before
+// the first output's reduction.
+template <class F, int LOGS, int MODE, bool BARRETT>
 __global__ void __launch_bounds__(kMatThreads, 1)
     ntt_matrix_pass_kernel(const MatrixPassArgs ma, const __grid_constant__ CUtensorMap in_map) {
   constexpr uint32_t S = 1u << LOGS;
@@ -657,14 +672,14 @@ __global__ void __launch_bounds__(kMatThreads, 1)
       uint64_t pos[2] = {0, 0};
       const uint64_t q = tile_q(u);
       const uint4 *offq = reinterpret_cast<const uint4 *>(ma.off_fold + q * S * 8);   // S entries of q
-      const bool new_off = ma.fold && ma.barrett && q != fac_q;
+      const bool new_off = BARRETT && ma.fold && q != fac_q;
       fac_q = q;
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         const uint32_t k = part + 4 * o;
         if (k < S && live) {
           pos[o] = mat_out_pos<LOGS, MODE>(a, d, k);
-          if (ma.fold && ma.barrett) {
+          if (BARRETT && ma.fold) {
             if (new_off) fe_load_global(fac[o], offq, k);
           } else if (ma.post) {
             fe_load_global(fac[o], ma.post, pos[o]);
@@ -675,42 +690,57 @@ __global__ void __launch_bounds__(kMatThreads, 1)
       }
       if (!mbar_wait(&acc_full[buf], (uint32_t)((it >> 1) & 1), ma, abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // each output in turn: its accumulators (back to the bias as they are
-      // read), ByteMerge, reduction, store
       constexpr int kOuts = S > 4 ? 2 : 1;
+      if constexpr (BARRETT) {
+        // output 0's accumulators, back to the bias, ByteMerge; output 1's
+        // load is issued into the same registers before output 0's Barrett
+        // reduction, so that its latency hides behind it
+        uint32_t r[32];
+        tmem_ld32(r, lane_addr + buf * NC + 32 * part);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int o = 0; o < kOuts; ++o) {
-        const uint32_t k = part + 4 * o;
-        if (k >= S) break;
-        uint32_t z[9];
-        {
-          uint32_t r[32];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-              : "r"(lane_addr + buf * NC + 32 * k));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int o = 0; o < kOuts; ++o) {
+          const uint32_t k = part + 4 * o;
+          if (k >= S) break;
+          if (o > 0) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           tmem_store_bias(lane_addr + buf * NC + 32 * k);   // for this buffer's next tile
-          if (ma.fold && ma.barrett) {
-            byte_merge(z, r, fac[o]);
-          } else if (ma.fold) {
-            uint32_t off[8];
-            fe_load_global(off, offq, k);
-            byte_merge(z, r, off);
-          } else {
-            byte_merge(z, r, ma.off[k]);
+          uint32_t z[9];
+          if (ma.fold) byte_merge(z, r, fac[o]);
+          else byte_merge(z, r, ma.off[k]);
+          if (o + 1 < kOuts && k + 4 < S) tmem_ld32(r, lane_addr + buf * NC + 32 * (k + 4));
+          if (live) {
+            uint32_t y[8];
+            barrett_z9<F>(y, z, ma.mu, lazy);
+            fe_store_global(a.dst, pos[o], y);
           }
         }
-        if (live) {
-          uint32_t y[8];
-          if (ma.barrett) barrett_z9<F>(y, z, ma.mu, lazy);
-          else mont_mul_z9<F>(y, z, fac[o], lazy);
-          fe_store_global(a.dst, pos[o], y);
+      } else {
+        // each output in turn: its accumulators (back to the bias as they
+        // are read), ByteMerge, Montgomery product, store -- one output's
+        // values live at a time
+#pragma unroll
+        for (int o = 0; o < kOuts; ++o) {
+          const uint32_t k = part + 4 * o;
+          if (k >= S) break;
+          uint32_t z[9];
+          {
+            uint32_t r[32];
+            tmem_ld32(r, lane_addr + buf * NC + 32 * k);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_store_bias(lane_addr + buf * NC + 32 * k);   // for this buffer's next tile
+            if (ma.fold) {
+              uint32_t off[8];
+              fe_load_global(off, offq, k);
+              byte_merge(z, r, off);
+            } else {
+              byte_merge(z, r, ma.off[k]);
+            }
+          }
+          if (live) {
+            uint32_t y[8];
+            mont_mul_z9<F>(y, z, fac[o], lazy);
+            fe_store_global(a.dst, pos[o], y);
+          }
         }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
