@@ -475,14 +475,20 @@ ntt_status ntt_pointwise_quotient(ntt_field field, const void *d_a, const void *
                                   ntt_stream stream);
 
 /*
- * Forward or inverse NTT of 2^log_n elements (1 <= log_n <= 24) over the
- * 377- or 753-bit field: element i is 12 (resp. 24) little-endian uint32
- * words at byte offset 48 i (resp. 96 i), standard form, canonical, natural
- * order; device buffers 16-byte aligned; d_in == d_out allowed.  Same pass
- * decomposition as the 256-bit transforms, with a generic-limb Montgomery
- * product.  The first call for a (device, field, log_n) builds the tables
- * on the device (synchronous; kept until the process exits).
- * Stream-ordered.  NTT_ERR_UNSUPPORTED for other kinds or sizes.
+ * NTT of 2^log_n elements (1 <= log_n <= 24) over the 377- or 753-bit
+ * field, any of the four kinds (forward, inverse, coset and coset inverse;
+ * the coset shift s is the field's generator, 7 resp. 11): element i is 12
+ * (resp. 24) little-endian uint32 words at byte offset 48 i (resp. 96 i),
+ * standard form, canonical, natural order; device buffers 16-byte aligned;
+ * d_in == d_out allowed.  Same pass decomposition as the 256-bit
+ * transforms, with a generic-limb Montgomery product; the coset factors
+ * s^i ride on the first pass's loads and the coset inverse's s^-i on the
+ * last pass's stores.  The first call for a (device, field, log_n) builds
+ * the tables on the device, and the first coset call of either coset kind
+ * the two coset tables (2 * 4 * LP * 2^log_n bytes, LP = 16 resp. 28);
+ * both synchronous, kept until the process exits.  Stream-ordered.
+ * NTT_ERR_INVALID_ARG for another field or kind, or unaligned or null
+ * buffers; NTT_ERR_UNSUPPORTED for other sizes.
  */
 ntt_status ntt_wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, const void *d_in, void *d_out,
                               ntt_stream stream);

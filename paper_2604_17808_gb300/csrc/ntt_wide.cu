@@ -100,6 +100,9 @@ struct WidePlan {
   uint4 *tw[2][kMaxPasses] = {};
   uint4 *pre_inv = nullptr;
   uint4 *scratch = nullptr;
+  uint4 *coset_pre = nullptr;    // s^i, i < N: first-pass input factors of the coset forward kind
+  uint4 *coset_post = nullptr;   // s^-i, i < N: last-pass output factors of the coset inverse kind
+  uint32_t *kbuf = nullptr;      // constants scratch of the table builders
   std::vector<void *> allocs;
 };
 
@@ -147,6 +150,7 @@ ntt_status build_wide(int field, uint32_t log_n, WidePlan *w) {
   uint32_t *kbuf = nullptr;
   if (cudaMalloc(&kbuf, 66 * 4 * L) != cudaSuccess) return NTT_ERR_OOM;
   w->allocs.push_back(kbuf);
+  w->kbuf = kbuf;
   cudaStream_t st = nullptr;
   for (uint32_t j = 0; j < P; ++j) {
     const uint32_t logs = w->pass_log[j];
@@ -173,6 +177,28 @@ ntt_status build_wide(int field, uint32_t log_n, WidePlan *w) {
   }
   if (P > 1) NTT_TRY_W(alloc_w(w, &w->scratch, (1ull << log_n) * 4ull * NL32));   // memory-layout elements
   return cuda_w(cudaDeviceSynchronize());
+}
+
+// The coset tables of the generator shift s, built on the first coset call
+// for this (device, field, size): s^i and s^-i for i < N.
+template <int NL32>
+ntt_status build_wide_coset(WidePlan *w) {
+  constexpr int L = WideShape<NL32>::L, LP = WideShape<NL32>::LP;
+  const uint64_t n = 1ull << w->log_n, eb = 4ull * LP;
+  uint4 *pre = nullptr, *post = nullptr;
+  NTT_TRY_W(alloc_w(w, &pre, n * eb));
+  NTT_TRY_W(alloc_w(w, &post, n * eb));
+  cudaStream_t st = nullptr;
+  wide_coset_constants_kernel<NL32><<<1, 1, 0, st>>>(w->kbuf);
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 152ull * 32) blocks = 152ull * 32;
+  wide_table_kernel<NL32><<<(unsigned)blocks, 256, 0, st>>>(pre, 0, w->kbuf, w->kbuf + 65 * L, n, 0);
+  wide_table_kernel<NL32><<<(unsigned)blocks, 256, 0, st>>>(post, 0, w->kbuf + 32 * L, w->kbuf + 65 * L, n, 0);
+  NTT_TRY_W(cuda_w(cudaGetLastError()));
+  NTT_TRY_W(cuda_w(cudaDeviceSynchronize()));
+  w->coset_pre = pre;
+  w->coset_post = post;
+  return NTT_OK;
 }
 
 template <int NL, int LOGS>
@@ -235,7 +261,7 @@ cudaError_t wide_dispatch(int logs, int mode, const PassArgs &a, uint64_t tiles,
   }
 }
 
-ntt_status wide_plan(int field, uint32_t log_n, WidePlan **out) {
+ntt_status wide_plan(int field, uint32_t log_n, bool coset, WidePlan **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_NO_DEVICE;
   if (dev < 0 || dev >= 8) return NTT_ERR_UNSUPPORTED;
@@ -251,19 +277,30 @@ ntt_status wide_plan(int field, uint32_t log_n, WidePlan **out) {
   }
   auto key = std::make_tuple(dev, field, log_n);
   auto it = g_wide_plans.find(key);
+  WidePlan *w = nullptr;
   if (it != g_wide_plans.end()) {
-    *out = it->second;
-    return NTT_OK;
+    w = it->second;
+  } else {
+    w = new (std::nothrow) WidePlan();
+    if (!w) return NTT_ERR_OOM;
+    const ntt_status s = limbs_of(field) == 12 ? build_wide<12>(field, log_n, w) : build_wide<24>(field, log_n, w);
+    if (s != NTT_OK) {
+      for (void *p : w->allocs) cudaFree(p);
+      delete w;
+      return s;
+    }
+    g_wide_plans[key] = w;
   }
-  WidePlan *w = new (std::nothrow) WidePlan();
-  if (!w) return NTT_ERR_OOM;
-  const ntt_status s = limbs_of(field) == 12 ? build_wide<12>(field, log_n, w) : build_wide<24>(field, log_n, w);
-  if (s != NTT_OK) {
-    for (void *p : w->allocs) cudaFree(p);
-    delete w;
-    return s;
+  if (coset && !w->coset_post) {
+    // a failure leaves the plan as it was (forward and inverse still work)
+    const size_t kept = w->allocs.size();
+    const ntt_status s = limbs_of(field) == 12 ? build_wide_coset<12>(w) : build_wide_coset<24>(w);
+    if (s != NTT_OK) {
+      for (size_t i = kept; i < w->allocs.size(); ++i) cudaFree(w->allocs[i]);
+      w->allocs.resize(kept);
+      return s;
+    }
   }
-  g_wide_plans[key] = w;
   *out = w;
   return NTT_OK;
 }
@@ -289,15 +326,17 @@ ntt_status ntt_field_element_bytes(ntt_field field, uint32_t *bytes) {
 ntt_status ntt_wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, const void *d_in, void *d_out,
                               ntt_stream stream) {
   if (field != NTT_FIELD_W377 && field != NTT_FIELD_W753) return NTT_ERR_INVALID_ARG;
-  if (kind != NTT_KIND_FORWARD && kind != NTT_KIND_INVERSE) return NTT_ERR_UNSUPPORTED;
+  if (kind != NTT_KIND_FORWARD && kind != NTT_KIND_INVERSE && kind != NTT_KIND_COSET && kind != NTT_KIND_COSET_INVERSE)
+    return NTT_ERR_INVALID_ARG;
   if (log_n < 1 || log_n > 24) return NTT_ERR_UNSUPPORTED;
   if (!d_in || !d_out || ((uintptr_t)d_in | (uintptr_t)d_out) % 16) return NTT_ERR_INVALID_ARG;
   WidePlan *w = nullptr;
-  const ntt_status s = wide_plan((int)field, log_n, &w);
+  const bool coset = kind == NTT_KIND_COSET || kind == NTT_KIND_COSET_INVERSE;
+  const ntt_status s = wide_plan((int)field, log_n, coset, &w);
   if (s != NTT_OK) return s;
   const int NL = limbs_of((int)field);
   const uint32_t TL = (uint32_t)tile_log((int)field);
-  const int dir = kind == NTT_KIND_INVERSE ? 1 : 0;
+  const int dir = (kind == NTT_KIND_INVERSE || kind == NTT_KIND_COSET_INVERSE) ? 1 : 0;
   const uint32_t P = w->num_passes;
   uint4 *work = (P > 1 && d_in == d_out) ? w->scratch : (uint4 *)d_out;
   for (uint32_t j = 0; j < P; ++j) {
@@ -317,7 +356,7 @@ ntt_status ntt_wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, co
         a.digit_shift[d - 1] = (uint8_t)shift;
         shift += w->pass_log[d];
       }
-      a.mul = (P == 1 && dir == 1) ? w->pre_inv : nullptr;
+      a.mul = kind == NTT_KIND_COSET ? w->coset_pre : (P == 1 && dir == 1) ? w->pre_inv : nullptr;
       mode = a.mul ? kModeFirstPre : kModeFirst;
     } else {
       uint32_t log_mp = 0;
@@ -328,6 +367,7 @@ ntt_status ntt_wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, co
       a.mul = w->tw[dir][j];
       mode = kModeInner;
     }
+    if (j == P - 1 && kind == NTT_KIND_COSET_INVERSE) a.post = w->coset_post;
     const uint64_t g = 1ull << (TL - logs);
     const uint64_t tiles = (a.num_sub + g - 1) / g;
     const cudaError_t e = NL == 12 ? wide_dispatch<12>((int)logs, mode, a, tiles, (cudaStream_t)stream)

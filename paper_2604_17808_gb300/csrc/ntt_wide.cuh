@@ -14,6 +14,12 @@
 // Tile: 2^TL elements in shared memory (29-bit limbs plus one padding word
 // per element: an odd stride keeps word accesses of consecutive elements
 // conflict-free), 256 threads, one radix-2 DIF stage per barrier.
+//
+// Multipliers: the first pass's table (mode kModeFirstPre) is indexed by
+// the input position (the coset factors s^i, or N^-1 for a one-pass
+// inverse), the inner passes' by (n, q) as in ntt_pass.cuh, and the
+// optional output table `post` by the output position (s^-i in the last
+// pass of a coset inverse).
 #pragma once
 
 #include <cstdint>
@@ -267,10 +273,11 @@ __global__ void __launch_bounds__(256, 2) wide_pass_kernel(const PassArgs a) {
       wide_load_tab<NL32>(w, a.mul, ((uint64_t)n << a.log_mp) + q);
       wide_mul<NL32>(v, v, w);
     } else {
-      wide_load_elem<NL32>(v, a.src, d + ((uint64_t)n << a.log_mp));
+      const uint64_t i = d + ((uint64_t)n << a.log_mp);   // input position
+      wide_load_elem<NL32>(v, a.src, i);
       if constexpr (MODE == kModeFirstPre) {
         uint32_t w[L];
-        wide_load_tab<NL32>(w, a.mul, n);
+        wide_load_tab<NL32>(w, a.mul, i);
         wide_mul<NL32>(v, v, w);
       }
     }
@@ -312,14 +319,26 @@ __global__ void __launch_bounds__(256, 2) wide_pass_kernel(const PassArgs a) {
       const uint64_t d = d0 + dl;
       if (d >= a.num_sub) continue;
       const uint64_t q = d & mp_mask, o = d >> a.log_mp;
+      const uint64_t pos = q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS));
       wide_tile_load<NL32>(v, tile, (dl << LOGS) | (__brev(k) >> (32 - LOGS)));
-      wide_store_elem<NL32>(a.dst, q + ((uint64_t)k << a.log_mp) + (o << (a.log_mp + LOGS)), v);
+      if (a.post) {   // output multipliers (uniform across the grid)
+        uint32_t w[L];
+        wide_load_tab<NL32>(w, a.post, pos);
+        wide_mul<NL32>(v, v, w);
+      }
+      wide_store_elem<NL32>(a.dst, pos, v);
     } else {
       const uint32_t dl = e >> LOGS, k = e & (S - 1);
       const uint64_t d = d0 + dl;
       if (d >= a.num_sub) continue;
+      const uint64_t pos = (reverse_digits(a, d) << LOGS) | k;
       wide_tile_load<NL32>(v, tile, (dl << LOGS) | (__brev(k) >> (32 - LOGS)));
-      wide_store_elem<NL32>(a.dst, (reverse_digits(a, d) << LOGS) | k, v);
+      if (a.post) {
+        uint32_t w[L];
+        wide_load_tab<NL32>(w, a.post, pos);
+        wide_mul<NL32>(v, v, w);
+      }
+      wide_store_elem<NL32>(a.dst, pos, v);
     }
   }
 }
@@ -392,6 +411,37 @@ __global__ void wide_constants_kernel(uint32_t *k, uint32_t log_m) {
   wide_from_words<NL32>(mi, mw);
   wide_mul<NL32>(mi, mi, C.r2);
   for (int j = 0; j < L; ++j) k[64 * L + j] = mi[j];
+  for (int j = 0; j < L; ++j) k[65 * L + j] = C.one[j];
+}
+
+// The coset shift s (the field's generator), for wide_table_kernel: writes
+//   k[0..31]  s^(2^b)     k[32..63]  s^-(2^b)     k[65]  R mod p (one)
+// (Montgomery form; s^-1 = s^(p-2) by Fermat's little theorem).  One thread.
+template <int NL32>
+__global__ void wide_coset_constants_kernel(uint32_t *k) {
+  constexpr int L = WideShape<NL32>::L;
+  const WideConst<NL32> &C = wide_const<NL32>();
+  uint32_t s[L], w[L];
+  for (int j = 0; j < L; ++j) s[j] = j == 0 ? C.gen : 0u;
+  wide_mul<NL32>(s, s, C.r2);
+  uint32_t em2[NL32];   // p - 2
+  int64_t br = -2;
+  for (int j = 0; j < NL32; ++j) {
+    const int64_t v = (int64_t)C.p32[j] + br;
+    em2[j] = (uint32_t)v;
+    br = v >> 32;
+  }
+  uint32_t inv[L];
+  wide_pow<NL32>(inv, s, em2, NL32);
+  for (int j = 0; j < L; ++j) w[j] = s[j];
+  for (int b = 0; b < 32; ++b) {
+    for (int j = 0; j < L; ++j) k[b * L + j] = w[j];
+    wide_mul<NL32>(w, w, w);
+  }
+  for (int b = 0; b < 32; ++b) {
+    for (int j = 0; j < L; ++j) k[(32 + b) * L + j] = inv[j];
+    wide_mul<NL32>(inv, inv, inv);
+  }
   for (int j = 0; j < L; ++j) k[65 * L + j] = C.one[j];
 }
 

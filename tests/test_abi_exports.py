@@ -53,6 +53,17 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert h.value is None
 
 
+def test_wide_transform_rejects_bad_arguments_without_touching_the_gpu(lib):
+    buf = (ctypes.c_uint64 * 64)()
+    p = ctypes.addressof(buf)
+    assert lib.ntt_wide_transform(0, 0, 4, p, p, None) == 1    # a 256-bit field: use the plans
+    assert lib.ntt_wide_transform(2, 4, 4, p, p, None) == 1    # no such kind
+    assert lib.ntt_wide_transform(3, 0, 0, p, p, None) == 2    # sizes 2^1 .. 2^24
+    assert lib.ntt_wide_transform(3, 3, 25, p, p, None) == 2
+    assert lib.ntt_wide_transform(2, 2, 4, None, p, None) == 1
+    assert lib.ntt_wide_transform(2, 2, 4, p + 8, p, None) == 1  # 16-byte alignment
+
+
 def test_null_plan_calls_are_rejected(lib):
     assert lib.ntt_forward(None, None, None, None) == 1
     assert lib.ntt_execute(None, 0, None, None, None) == 1

@@ -1,8 +1,10 @@
 """GPU parity of the 377- and 753-bit transforms (ntt_wide_transform) with
 the Python oracle: every size from 2^1 to 2^13 (one and two passes, ragged
-splits) forward and inverse element by element, in place, and at 2^16 and
-2^20 the exact round trip plus outputs the oracle evaluates one by one
-(Horner at omega^k).  The bar is bit-exact."""
+splits) in all four kinds (forward, inverse, coset, coset inverse) element
+by element, in place, and at 2^16 and 2^20 the exact round trips plus
+outputs the oracle evaluates one by one (Horner at omega^k and at
+s omega^k; the coset inverse at omega^-n, scaled by s^-n N^-1).  The bar
+is bit-exact."""
 
 from __future__ import annotations
 
@@ -62,12 +64,33 @@ def test_all_small_sizes_match_oracle(field):
 
 
 @pytest.mark.parametrize("field", FIELDS)
+def test_coset_kinds_all_small_sizes_match_oracle(field):
+    f = O.get_field(field)
+    for log_n in range(1, 14):
+        x = uniform_elements(field, 1 << log_n, 64300 + log_n)
+        d_x = dev(x)
+        d_y = torch.empty_like(d_x)
+        N.ntt_wide_transform(field, "coset", log_n, d_x, d_y)
+        assert ints(host(d_y), field) == O.coset_ntt(f, ints(x, field)), ("coset", log_n)
+        N.ntt_wide_transform(field, "coset_inverse", log_n, d_x, d_y)
+        assert ints(host(d_y), field) == O.coset_intt(f, ints(x, field)), ("coset_inverse", log_n)
+        # the plain kinds of the same size still agree after the coset tables exist
+        N.ntt_wide_transform(field, "forward", log_n, d_x, d_y)
+        assert ints(host(d_y), field) == O.ntt(f, ints(x, field)), ("forward after coset", log_n)
+
+
+@pytest.mark.parametrize("field", FIELDS)
 def test_in_place_round_trip(field):
     log_n = 14
     x = uniform_elements(field, 1 << log_n, 64100)
     d = dev(x)
     N.ntt_wide_transform(field, "forward", log_n, d, d)
     N.ntt_wide_transform(field, "inverse", log_n, d, d)
+    assert np.array_equal(host(d), x)
+    f = O.get_field(field)
+    N.ntt_wide_transform(field, "coset", log_n, d, d)
+    assert ints(host(d), field) == O.coset_ntt(f, ints(x, field))
+    N.ntt_wide_transform(field, "coset_inverse", log_n, d, d)
     assert np.array_equal(host(d), x)
 
 
@@ -90,13 +113,29 @@ def test_large_sizes_round_trip_and_sampled_outputs(field, log_n):
     got = ints(host(d_y)[ks], field)
     for k, v in zip(ks, got):
         assert v == O.horner(f, xs, pow(w, k, f.modulus)), k
+    # coset kinds: X_k = x(s omega^k); the coset inverse of x gives
+    # s^-m N^-1 x(omega^-m) at position m, and the pair is the identity
+    M = f.modulus
+    s = O.default_coset_shift(f)
+    N.ntt_wide_transform(field, "coset", log_n, d_x, d_y)
+    N.ntt_wide_transform(field, "coset_inverse", log_n, d_y, d_z)
+    assert torch.equal(d_z, d_x)
+    got = ints(host(d_y)[ks], field)
+    for k, v in zip(ks, got):
+        assert v == O.horner(f, xs, s * pow(w, k, M) % M), ("coset", k)
+    N.ntt_wide_transform(field, "coset_inverse", log_n, d_x, d_y)
+    got = ints(host(d_y)[ks], field)
+    n_inv, s_inv, w_inv = O.inverse(f, n), O.inverse(f, s), O.inverse(f, w)
+    for m, v in zip(ks, got):
+        want = O.horner(f, xs, pow(w_inv, m, M)) * n_inv % M * pow(s_inv, m, M) % M
+        assert v == want, ("coset_inverse", m)
 
 
 def test_wide_argument_errors():
     x = torch.zeros((64, 12), dtype=torch.int64, device="cuda")
     with pytest.raises(N.NttError) as e:
-        N.ntt_wide_transform("w753", "coset", 6, x, x)
-    assert e.value.status == 2
+        N.ntt_wide_transform("w753", 4, 6, x, x)
+    assert e.value.status == 1
     with pytest.raises(N.NttError):
         N.ntt_wide_transform("w753", "forward", 25, x, x)
     with pytest.raises(N.NttError):
