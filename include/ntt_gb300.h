@@ -486,12 +486,27 @@ ntt_status ntt_pointwise_quotient(ntt_field field, const void *d_a, const void *
  * last pass's stores.  The first call for a (device, field, log_n) builds
  * the tables on the device, and the first coset call of either coset kind
  * the two coset tables (2 * 4 * LP * 2^log_n bytes, LP = 16 resp. 28);
- * both synchronous, kept until the process exits.  Stream-ordered.
+ * both synchronous, kept until the process exits.  Stream-ordered.  The
+ * tables and an in-place call's scratch vector belong to the (device,
+ * field, log_n), not to the caller: two in-place calls of the same field
+ * and size must not run at the same time on different streams.
  * NTT_ERR_INVALID_ARG for another field or kind, or unaligned or null
  * buffers; NTT_ERR_UNSUPPORTED for other sizes.
  */
 ntt_status ntt_wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, const void *d_in, void *d_out,
                               ntt_stream stream);
+/*
+ * The coset kinds of ntt_wide_transform with a caller-chosen shift s:
+ * h_shift points to 12 (377-bit) or 24 (753-bit) little-endian uint32 words
+ * in host memory, standard form, 0 < s < p; kind is NTT_KIND_COSET or
+ * NTT_KIND_COSET_INVERSE.  The (device, field, log_n) keeps the coset
+ * tables of one shift: a call with another shift than the last one waits
+ * for the device to be idle (cudaDeviceSynchronize), rewrites the tables
+ * and then enqueues its transform.  NTT_ERR_INVALID_ARG for a null, zero or
+ * out-of-range shift, another kind, or the errors of ntt_wide_transform.
+ */
+ntt_status ntt_wide_transform_shift(ntt_field field, ntt_kind kind, uint32_t log_n, const uint32_t *h_shift,
+                                    const void *d_in, void *d_out, ntt_stream stream);
 /* Bytes of one element of `field` in memory (32, 32, 48, 96). */
 ntt_status ntt_field_element_bytes(ntt_field field, uint32_t *bytes);
 

@@ -114,6 +114,8 @@ _SIGS = {
     "ntt_field_mont_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _VP]),
     "ntt_rns_basis_get": (ctypes.c_int, [ctypes.c_int, _VP]),
     "ntt_wide_transform": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _U32, _VP, _VP, _VP]),
+    "ntt_wide_transform_shift": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _U32, ctypes.POINTER(_U32), _VP, _VP,
+                                                _VP]),
     "ntt_field_element_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_U32)]),
     "ntt_rns_mul": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _U64, _U32, _VP]),
     "ntt_rns_poll_error": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_U32)]),
@@ -374,9 +376,20 @@ def ntt_pointwise_quotient(field, d_a, d_b, d_c, z_values, d_out, count: int, st
                                          int(count), _stream(stream)), "ntt_pointwise_quotient")
 
 
-def ntt_wide_transform(field, kind, log_n: int, d_in, d_out, stream=None) -> None:
-    _check(load().ntt_wide_transform(_field(field), _kind(kind), int(log_n), _ptr(d_in), _ptr(d_out),
-                                     _stream(stream)), "ntt_wide_transform")
+def ntt_wide_transform(field, kind, log_n: int, d_in, d_out, stream=None, shift: int | None = None) -> None:
+    """377/753-bit transform; ``shift`` (an int, coset kinds only) replaces
+    the generator as the coset shift."""
+    if shift is None:
+        _check(load().ntt_wide_transform(_field(field), _kind(kind), int(log_n), _ptr(d_in), _ptr(d_out),
+                                         _stream(stream)), "ntt_wide_transform")
+        return
+    words = 12 if _field(field) == FIELD["w377"] else 24
+    s = int(shift)
+    if s < 0 or s >= 1 << (32 * words):
+        raise ValueError("shift does not fit the field's words")
+    arr = (_U32 * 24)(*[(s >> (32 * i)) & 0xFFFFFFFF for i in range(24)])
+    _check(load().ntt_wide_transform_shift(_field(field), _kind(kind), int(log_n), arr, _ptr(d_in), _ptr(d_out),
+                                           _stream(stream)), "ntt_wide_transform_shift")
 
 
 def ntt_field_element_bytes(field) -> int:

@@ -102,6 +102,8 @@ struct WidePlan {
   uint4 *scratch = nullptr;
   uint4 *coset_pre = nullptr;    // s^i, i < N: first-pass input factors of the coset forward kind
   uint4 *coset_post = nullptr;   // s^-i, i < N: last-pass output factors of the coset inverse kind
+  uint32_t coset_shift[24] = {}; // the s of those tables (32-bit words, standard form)
+  bool coset_ready = false;      // the two tables hold the powers of coset_shift
   uint32_t *kbuf = nullptr;      // constants scratch of the table builders
   std::vector<void *> allocs;
 };
@@ -179,16 +181,33 @@ ntt_status build_wide(int field, uint32_t log_n, WidePlan *w) {
   return cuda_w(cudaDeviceSynchronize());
 }
 
-// The coset tables of the generator shift s, built on the first coset call
-// for this (device, field, size): s^i and s^-i for i < N.
+// The coset tables of shift s (NL32 words, 0 < s < p), s^i and s^-i for
+// i < N: allocated on the first coset call for this (device, field, size),
+// rewritten in place when a call brings another shift (after the device is
+// idle: transforms enqueued earlier may still read the old tables).
 template <int NL32>
-ntt_status build_wide_coset(WidePlan *w) {
+ntt_status build_wide_coset(WidePlan *w, const uint32_t *shift) {
   constexpr int L = WideShape<NL32>::L, LP = WideShape<NL32>::LP;
   const uint64_t n = 1ull << w->log_n, eb = 4ull * LP;
-  uint4 *pre = nullptr, *post = nullptr;
-  NTT_TRY_W(alloc_w(w, &pre, n * eb));
-  NTT_TRY_W(alloc_w(w, &post, n * eb));
+  if (!w->coset_post) {
+    const size_t kept = w->allocs.size();
+    uint4 *pre = nullptr, *post = nullptr;
+    ntt_status s = alloc_w(w, &pre, n * eb);
+    if (s == NTT_OK) s = alloc_w(w, &post, n * eb);
+    if (s != NTT_OK) {   // forward and inverse stay usable
+      for (size_t i = kept; i < w->allocs.size(); ++i) cudaFree(w->allocs[i]);
+      w->allocs.resize(kept);
+      return s;
+    }
+    w->coset_pre = pre;
+    w->coset_post = post;
+  } else {
+    NTT_TRY_W(cuda_w(cudaDeviceSynchronize()));
+  }
+  w->coset_ready = false;   // until the tables below are written
+  uint4 *pre = w->coset_pre, *post = w->coset_post;
   cudaStream_t st = nullptr;
+  NTT_TRY_W(cuda_w(cudaMemcpy(w->kbuf + 64 * L, shift, 4 * NL32, cudaMemcpyHostToDevice)));
   wide_coset_constants_kernel<NL32><<<1, 1, 0, st>>>(w->kbuf);
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 152ull * 32) blocks = 152ull * 32;
@@ -196,8 +215,8 @@ ntt_status build_wide_coset(WidePlan *w) {
   wide_table_kernel<NL32><<<(unsigned)blocks, 256, 0, st>>>(post, 0, w->kbuf + 32 * L, w->kbuf + 65 * L, n, 0);
   NTT_TRY_W(cuda_w(cudaGetLastError()));
   NTT_TRY_W(cuda_w(cudaDeviceSynchronize()));
-  w->coset_pre = pre;
-  w->coset_post = post;
+  std::memcpy(w->coset_shift, shift, 4 * NL32);
+  w->coset_ready = true;
   return NTT_OK;
 }
 
@@ -261,11 +280,14 @@ cudaError_t wide_dispatch(int logs, int mode, const PassArgs &a, uint64_t tiles,
   }
 }
 
-ntt_status wide_plan(int field, uint32_t log_n, bool coset, WidePlan **out) {
+// The (device, field, size) tables, built on first use; with a shift
+// (NL32 words), also the coset tables of that shift.  The caller holds
+// g_wide_mu until its transform is enqueued, so no other call can rewrite
+// the coset tables in between.
+ntt_status wide_plan(int field, uint32_t log_n, const uint32_t *shift, WidePlan **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NTT_ERR_NO_DEVICE;
   if (dev < 0 || dev >= 8) return NTT_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_wide_mu);
   if (!g_wide_ready[dev]) {
     const WideConst<12> c12 = make_const<12>(kP377, 7);
     const WideConst<24> c24 = make_const<24>(kP753, 11);
@@ -291,17 +313,76 @@ ntt_status wide_plan(int field, uint32_t log_n, bool coset, WidePlan **out) {
     }
     g_wide_plans[key] = w;
   }
-  if (coset && !w->coset_post) {
-    // a failure leaves the plan as it was (forward and inverse still work)
-    const size_t kept = w->allocs.size();
-    const ntt_status s = limbs_of(field) == 12 ? build_wide_coset<12>(w) : build_wide_coset<24>(w);
-    if (s != NTT_OK) {
-      for (size_t i = kept; i < w->allocs.size(); ++i) cudaFree(w->allocs[i]);
-      w->allocs.resize(kept);
-      return s;
-    }
+  if (shift && (!w->coset_ready || std::memcmp(w->coset_shift, shift, 4 * limbs_of(field)) != 0)) {
+    // a failure leaves forward and inverse usable and the coset tables
+    // marked unwritten (the next coset call writes them again)
+    NTT_TRY_W(limbs_of(field) == 12 ? build_wide_coset<12>(w, shift) : build_wide_coset<24>(w, shift));
   }
   *out = w;
+  return NTT_OK;
+}
+
+// 0 < s < p for a shift of NL32 little-endian words.
+bool shift_in_range(ntt_field field, const uint32_t *sw) {
+  const int nl = limbs_of((int)field);
+  const uint32_t *p = field == NTT_FIELD_W377 ? kP377 : kP753;
+  bool zero = true;
+  for (int j = 0; j < nl; ++j) zero = zero && sw[j] == 0;
+  if (zero) return false;
+  for (int j = nl - 1; j >= 0; --j)
+    if (sw[j] != p[j]) return sw[j] < p[j];
+  return false;   // s == p
+}
+
+// One transform; `shift` (NL32 words, checked by the caller) is used by the
+// coset kinds only.  The table lock is held until every pass is enqueued.
+ntt_status wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, const uint32_t *shift, const void *d_in,
+                          void *d_out, ntt_stream stream) {
+  std::lock_guard<std::mutex> lk(g_wide_mu);
+  WidePlan *w = nullptr;
+  const bool coset = kind == NTT_KIND_COSET || kind == NTT_KIND_COSET_INVERSE;
+  const ntt_status s = wide_plan((int)field, log_n, coset ? shift : nullptr, &w);
+  if (s != NTT_OK) return s;
+  const int NL = limbs_of((int)field);
+  const uint32_t TL = (uint32_t)tile_log((int)field);
+  const int dir = (kind == NTT_KIND_INVERSE || kind == NTT_KIND_COSET_INVERSE) ? 1 : 0;
+  const uint32_t P = w->num_passes;
+  uint4 *work = (P > 1 && d_in == d_out) ? w->scratch : (uint4 *)d_out;
+  for (uint32_t j = 0; j < P; ++j) {
+    const uint32_t logs = w->pass_log[j];
+    PassArgs a{};
+    a.dft_tw = w->dft_tw[dir][logs];
+    a.num_sub = 1ull << (log_n - logs);
+    int mode;
+    if (j == 0) {
+      a.src = (const uint4 *)d_in;
+      a.dst = P == 1 ? (uint4 *)d_out : work;
+      a.log_mp = log_n - logs;
+      a.num_digits = P - 1;
+      uint32_t dshift = 0;
+      for (uint32_t d = 1; d < P; ++d) {
+        a.digit_log[d - 1] = (uint8_t)w->pass_log[d];
+        a.digit_shift[d - 1] = (uint8_t)dshift;
+        dshift += w->pass_log[d];
+      }
+      a.mul = kind == NTT_KIND_COSET ? w->coset_pre : (P == 1 && dir == 1) ? w->pre_inv : nullptr;
+      mode = a.mul ? kModeFirstPre : kModeFirst;
+    } else {
+      uint32_t log_mp = 0;
+      for (uint32_t i = 0; i < j; ++i) log_mp += w->pass_log[i];
+      a.src = work;
+      a.dst = j == P - 1 ? (uint4 *)d_out : work;
+      a.log_mp = log_mp;
+      a.mul = w->tw[dir][j];
+      mode = kModeInner;
+    }
+    if (j == P - 1 && kind == NTT_KIND_COSET_INVERSE) a.post = w->coset_post;
+    const uint64_t g = 1ull << (TL - logs);
+    const uint64_t tiles = (a.num_sub + g - 1) / g;
+    const cudaError_t e = NL == 12 ? wide_dispatch<12>((int)logs, mode, a, tiles, (cudaStream_t)stream)
+                                   : wide_dispatch<24>((int)logs, mode, a, tiles, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   return NTT_OK;
 }
 
@@ -330,51 +411,18 @@ ntt_status ntt_wide_transform(ntt_field field, ntt_kind kind, uint32_t log_n, co
     return NTT_ERR_INVALID_ARG;
   if (log_n < 1 || log_n > 24) return NTT_ERR_UNSUPPORTED;
   if (!d_in || !d_out || ((uintptr_t)d_in | (uintptr_t)d_out) % 16) return NTT_ERR_INVALID_ARG;
-  WidePlan *w = nullptr;
-  const bool coset = kind == NTT_KIND_COSET || kind == NTT_KIND_COSET_INVERSE;
-  const ntt_status s = wide_plan((int)field, log_n, coset, &w);
-  if (s != NTT_OK) return s;
-  const int NL = limbs_of((int)field);
-  const uint32_t TL = (uint32_t)tile_log((int)field);
-  const int dir = (kind == NTT_KIND_INVERSE || kind == NTT_KIND_COSET_INVERSE) ? 1 : 0;
-  const uint32_t P = w->num_passes;
-  uint4 *work = (P > 1 && d_in == d_out) ? w->scratch : (uint4 *)d_out;
-  for (uint32_t j = 0; j < P; ++j) {
-    const uint32_t logs = w->pass_log[j];
-    PassArgs a{};
-    a.dft_tw = w->dft_tw[dir][logs];
-    a.num_sub = 1ull << (log_n - logs);
-    int mode;
-    if (j == 0) {
-      a.src = (const uint4 *)d_in;
-      a.dst = P == 1 ? (uint4 *)d_out : work;
-      a.log_mp = log_n - logs;
-      a.num_digits = P - 1;
-      uint32_t shift = 0;
-      for (uint32_t d = 1; d < P; ++d) {
-        a.digit_log[d - 1] = (uint8_t)w->pass_log[d];
-        a.digit_shift[d - 1] = (uint8_t)shift;
-        shift += w->pass_log[d];
-      }
-      a.mul = kind == NTT_KIND_COSET ? w->coset_pre : (P == 1 && dir == 1) ? w->pre_inv : nullptr;
-      mode = a.mul ? kModeFirstPre : kModeFirst;
-    } else {
-      uint32_t log_mp = 0;
-      for (uint32_t i = 0; i < j; ++i) log_mp += w->pass_log[i];
-      a.src = work;
-      a.dst = j == P - 1 ? (uint4 *)d_out : work;
-      a.log_mp = log_mp;
-      a.mul = w->tw[dir][j];
-      mode = kModeInner;
-    }
-    if (j == P - 1 && kind == NTT_KIND_COSET_INVERSE) a.post = w->coset_post;
-    const uint64_t g = 1ull << (TL - logs);
-    const uint64_t tiles = (a.num_sub + g - 1) / g;
-    const cudaError_t e = NL == 12 ? wide_dispatch<12>((int)logs, mode, a, tiles, (cudaStream_t)stream)
-                                   : wide_dispatch<24>((int)logs, mode, a, tiles, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_status(e);
-  }
-  return NTT_OK;
+  uint32_t gen[24] = {field == NTT_FIELD_W377 ? 7u : 11u};   // the default shift: the generator
+  return wide_transform(field, kind, log_n, gen, d_in, d_out, stream);
+}
+
+ntt_status ntt_wide_transform_shift(ntt_field field, ntt_kind kind, uint32_t log_n, const uint32_t *h_shift,
+                                    const void *d_in, void *d_out, ntt_stream stream) {
+  if (field != NTT_FIELD_W377 && field != NTT_FIELD_W753) return NTT_ERR_INVALID_ARG;
+  if (kind != NTT_KIND_COSET && kind != NTT_KIND_COSET_INVERSE) return NTT_ERR_INVALID_ARG;
+  if (log_n < 1 || log_n > 24) return NTT_ERR_UNSUPPORTED;
+  if (!d_in || !d_out || ((uintptr_t)d_in | (uintptr_t)d_out) % 16) return NTT_ERR_INVALID_ARG;
+  if (!h_shift || !shift_in_range(field, h_shift)) return NTT_ERR_INVALID_ARG;
+  return wide_transform(field, kind, log_n, h_shift, d_in, d_out, stream);
 }
 
 }  // extern "C"

@@ -414,7 +414,8 @@ __global__ void wide_constants_kernel(uint32_t *k, uint32_t log_m) {
   for (int j = 0; j < L; ++j) k[65 * L + j] = C.one[j];
 }
 
-// The coset shift s (the field's generator), for wide_table_kernel: writes
+// The coset shift s for wide_table_kernel.  Reads s from k[64] (NL32
+// 32-bit words, standard form, 0 < s < p: the host checks) and writes
 //   k[0..31]  s^(2^b)     k[32..63]  s^-(2^b)     k[65]  R mod p (one)
 // (Montgomery form; s^-1 = s^(p-2) by Fermat's little theorem).  One thread.
 template <int NL32>
@@ -422,7 +423,11 @@ __global__ void wide_coset_constants_kernel(uint32_t *k) {
   constexpr int L = WideShape<NL32>::L;
   const WideConst<NL32> &C = wide_const<NL32>();
   uint32_t s[L], w[L];
-  for (int j = 0; j < L; ++j) s[j] = j == 0 ? C.gen : 0u;
+  {
+    uint32_t sw[NL32];
+    for (int j = 0; j < NL32; ++j) sw[j] = k[64 * L + j];
+    wide_from_words<NL32>(s, sw);
+  }
   wide_mul<NL32>(s, s, C.r2);
   uint32_t em2[NL32];   // p - 2
   int64_t br = -2;

@@ -64,6 +64,21 @@ def test_wide_transform_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.ntt_wide_transform(2, 2, 4, p + 8, p, None) == 1  # 16-byte alignment
 
 
+def test_wide_shift_is_checked_without_touching_the_gpu(lib):
+    buf = (ctypes.c_uint64 * 64)()
+    p = ctypes.addressof(buf)
+    W = ctypes.c_uint32 * 24
+    p377 = 0x1921FB54442D18469898CC51701B839A252049C1114CF98E804177D4C76273644A29410F31C6809BBDF2BD500000001
+    words = lambda v: W(*[(v >> (32 * i)) & 0xFFFFFFFF for i in range(24)])  # noqa: E731
+    assert lib.ntt_wide_transform_shift(2, 2, 4, None, p, p, None) == 1             # no shift
+    assert lib.ntt_wide_transform_shift(2, 2, 4, words(0), p, p, None) == 1         # s = 0
+    assert lib.ntt_wide_transform_shift(2, 3, 4, words(p377), p, p, None) == 1      # s = p
+    assert lib.ntt_wide_transform_shift(2, 3, 4, words(p377 + 5), p, p, None) == 1  # s > p
+    assert lib.ntt_wide_transform_shift(2, 0, 4, words(3), p, p, None) == 1         # not a coset kind
+    assert lib.ntt_wide_transform_shift(0, 2, 4, words(3), p, p, None) == 1         # a 256-bit field
+    assert lib.ntt_wide_transform_shift(3, 2, 0, words(3), p, p, None) == 2
+
+
 def test_null_plan_calls_are_rejected(lib):
     assert lib.ntt_forward(None, None, None, None) == 1
     assert lib.ntt_execute(None, 0, None, None, None) == 1

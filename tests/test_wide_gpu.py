@@ -1,10 +1,10 @@
 """GPU parity of the 377- and 753-bit transforms (ntt_wide_transform) with
 the Python oracle: every size from 2^1 to 2^13 (one and two passes, ragged
 splits) in all four kinds (forward, inverse, coset, coset inverse) element
-by element, in place, and at 2^16 and 2^20 the exact round trips plus
-outputs the oracle evaluates one by one (Horner at omega^k and at
-s omega^k; the coset inverse at omega^-n, scaled by s^-n N^-1).  The bar
-is bit-exact."""
+by element, the coset kinds also with caller-chosen shifts; in place; and
+at 2^16 and 2^20 the exact round trips plus outputs the oracle evaluates
+one by one (Horner at omega^k and at s omega^k; the coset inverse at
+omega^-n, scaled by s^-n N^-1).  The bar is bit-exact."""
 
 from __future__ import annotations
 
@@ -129,6 +129,35 @@ def test_large_sizes_round_trip_and_sampled_outputs(field, log_n):
     for m, v in zip(ks, got):
         want = O.horner(f, xs, pow(w_inv, m, M)) * n_inv % M * pow(s_inv, m, M) % M
         assert v == want, ("coset_inverse", m)
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_custom_coset_shift_matches_oracle(field):
+    f = O.get_field(field)
+    M = f.modulus
+    rng = random.Random(64400)
+    shifts = [3, rng.randrange(2, M)]
+    for log_n in (5, 12, 14):
+        x = uniform_elements(field, 1 << log_n, 64400 + log_n)
+        xs = ints(x, field)
+        d_x = dev(x)
+        d_y = torch.empty_like(d_x)
+        for s in shifts + [shifts[0]]:   # a change of shift, and back
+            N.ntt_wide_transform(field, "coset", log_n, d_x, d_y, shift=s)
+            assert ints(host(d_y), field) == O.coset_ntt(f, xs, s), ("coset", log_n, s)
+            N.ntt_wide_transform(field, "coset_inverse", log_n, d_x, d_y, shift=s)
+            assert ints(host(d_y), field) == O.coset_intt(f, xs, s), ("coset_inverse", log_n, s)
+        # the default call goes back to the generator
+        N.ntt_wide_transform(field, "coset", log_n, d_x, d_y)
+        assert ints(host(d_y), field) == O.coset_ntt(f, xs), ("coset, generator", log_n)
+        # an explicit shift equal to the generator is the default transform
+        N.ntt_wide_transform(field, "coset_inverse", log_n, d_x, d_y, shift=f.generator)
+        assert ints(host(d_y), field) == O.coset_intt(f, xs), ("coset_inverse, generator", log_n)
+    x = torch.zeros((32, 2 * (6 if field == "w377" else 12)), dtype=torch.int64, device="cuda")
+    for bad in (0, M, M + 1):
+        with pytest.raises(N.NttError) as e:
+            N.ntt_wide_transform(field, "coset", 5, x, x, shift=bad)
+        assert e.value.status == 1
 
 
 def test_wide_argument_errors():
